@@ -1,0 +1,351 @@
+"""FP64 reference of the gradient-descent multislice ptychography path.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): plain, slow and
+obviously correct; complex128 throughout; every transform is a dense DFT
+written out as two matrix products.
+
+What it computes (arXiv 2505.14372):
+  * §3, multislice recurrence: the entry wave is the probe mode shifted to the
+    scan position; each slice multiplies by the object slice and, between
+    slices, convolves with the Fresnel kernel p(dz) (done as DFT, product with
+    the propagator, inverse DFT) under an anti-aliasing band limit.
+  * §3, far field: I(k) = sum over incoherent modes of |F(exit wave)|^2.
+  * §3.1, noise models: amplitude / Anscombe least squares on sqrt(I + c) and
+    the Poisson negative log-likelihood in Stirling form with an epsilon
+    inside the logarithms; the analytic detector-plane gradients of §3.1 are
+    what the seed of the adjoint reduces to.
+  * §3.2, gradient of the real loss with respect to every complex variable
+    (Wirtinger calculus), for all slices and modes at once, and the Adam
+    update applied to it.
+
+Readings taken where the paper is silent or ambiguous (each one is also
+listed in the design doc):
+  R1  S slices take S-1 propagations; nothing is propagated after the last.
+  R2  F is the unnormalised DFT with kernel exp(-2 pi i k x / N); F^-1 carries
+      1/N; the far field uses the orthonormal F/sqrt(N); no fftshift: the
+      zero frequency sits at pixel [0, 0] of every pattern.
+  R3  Fresnel propagator H(q) = B(q) exp(-i pi lambda dz |q|^2), with
+      q = f / (N dx) and f the integer DFT frequency in numpy fftfreq order
+      (the Nyquist bin of an even size is -N/2).  B is a circular band limit
+      at beta times the Nyquist frequency 1/(2 dx): on the discrete grid it
+      keeps (f_u w)^2 + (f_v h)^2 <= floor(x*x) with x = beta*h*w*0.5
+      evaluated left to right in IEEE double, so that the boundary decision
+      is an exact integer comparison.  beta <= 0 switches the band limit off.
+      The band limit acts in every propagation, not in the shift or far field.
+  R4  A scan position r = (y, x) is in object pixels and locates the window's
+      top-left corner.  n = floor(r + 1/2) picks the object patch and
+      delta = r - n in [-1/2, 1/2) is applied as the Fourier phase ramp
+      exp(-2 pi i (f_u delta_y / h + f_v delta_x / w)), i.e. P(r - delta).
+  R5  Amplitude (c = 0) / Anscombe (c = 3/8) loss per pixel:
+      l = 1/2 (sqrt(I + c + eps) - sqrt(I_exp + c + eps))^2.
+      Poisson loss per pixel: l = I - I_exp - I_exp (log(I+eps) - log(I_exp+eps)),
+      whose derivative 1 - I_exp/(I + eps) is exactly the paper's Poisson
+      detector gradient factor.
+  R6  The loss is the plain sum over pixels and positions.
+  R7  Gradient of a real L with respect to complex z is
+      dL/dRe z + i dL/dIm z (= 2 dL/d conj(z)), twice the paper's
+      conj(dL/dz); it matches finite differences on Re and Im directly.
+  R8  Complex Adam: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2)|g|^2 (real),
+      z <- z - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps_adam).
+  R9  Incoherent mode weights are carried by the mode amplitudes.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from functools import lru_cache
+
+import numpy as np
+
+AMPLITUDE = 0
+POISSON = 1
+
+__all__ = [
+    "AMPLITUDE", "POISSON", "Geom", "freq_index", "dft_matrix", "dft2",
+    "idft2", "dft2_ortho", "idft2_ortho", "split_positions", "shift_ramp",
+    "shift_probe", "bandlimit_mask", "propagator", "propagate",
+    "forward", "forward_waves", "loss_terms", "loss_value", "gradient",
+    "adam_update", "step", "position_gradient",
+]
+
+
+@dataclass
+class Geom:
+    """Problem geometry (§3): S slices, K probe modes, h x w window,
+    H x W object, pixel size dx [A], wavelength lam [A], S-1 gaps dz [A]."""
+    S: int
+    K: int
+    h: int
+    w: int
+    H: int
+    W: int
+    dx: float = 0.1
+    lam: float = 0.0197
+    dz: tuple = field(default_factory=tuple)
+    bandlimit: float = 2.0 / 3.0
+    loss: int = AMPLITUDE
+    eps: float = 0.0
+    c: float = 0.0
+
+    def __post_init__(self):
+        self.dz = tuple(float(z) for z in self.dz)
+        if len(self.dz) != max(self.S - 1, 0):
+            raise ValueError("need S-1 slice gaps")
+
+
+# ---------------------------------------------------------------- DFT (R2)
+
+def freq_index(n: int) -> np.ndarray:
+    """Integer DFT frequency of each bin in fftfreq order (R3)."""
+    u = np.arange(n)
+    return np.where(u < (n + 1) // 2, u, u - n)
+
+
+@lru_cache(maxsize=None)
+def dft_matrix(n: int) -> np.ndarray:
+    """Dense F[k, x] = exp(-2 pi i (k x mod n) / n), angles from exact
+    integer products."""
+    idx = np.arange(n, dtype=np.int64)
+    m = np.outer(idx, idx) % n
+    ang = 2.0 * np.pi * m.astype(np.float64) / n
+    F = np.cos(ang) - 1j * np.sin(ang)
+    F.setflags(write=False)
+    return F
+
+
+def dft2(x: np.ndarray) -> np.ndarray:
+    """Unnormalised 2-D DFT over the last two axes: F_h x F_w^T."""
+    h, w = x.shape[-2:]
+    return dft_matrix(h) @ x @ dft_matrix(w).T
+
+
+def idft2(X: np.ndarray) -> np.ndarray:
+    """Inverse of dft2 (carries 1/(h w))."""
+    h, w = X.shape[-2:]
+    return (np.conj(dft_matrix(h)) @ X @ np.conj(dft_matrix(w)).T) / (h * w)
+
+
+def dft2_ortho(x: np.ndarray) -> np.ndarray:
+    h, w = x.shape[-2:]
+    return dft2(x) / math.sqrt(h * w)
+
+
+def idft2_ortho(X: np.ndarray) -> np.ndarray:
+    h, w = X.shape[-2:]
+    return idft2(X) * math.sqrt(h * w)
+
+
+# ------------------------------------------------------ shift & gather (R4)
+
+def split_positions(pos) -> tuple[np.ndarray, np.ndarray]:
+    """Integer patch origin n = floor(r + 1/2) and subpixel part r - n."""
+    r = np.asarray(pos, dtype=np.float64).reshape(-1, 2)
+    n = np.floor(r + 0.5)
+    return n.astype(np.int64), r - n
+
+
+def shift_ramp(dy: float, dx_: float, h: int, w: int) -> np.ndarray:
+    """exp(-2 pi i (f_u dy / h + f_v dx / w)); the phase is formed in turns
+    and reduced to [-1/2, 1/2] before the exponential."""
+    t = (freq_index(h)[:, None] * float(dy) / h
+         + freq_index(w)[None, :] * float(dx_) / w)
+    t = t - np.round(t)
+    return np.exp(-2j * np.pi * t)
+
+
+def shift_probe(P: np.ndarray, dy: float, dx_: float) -> np.ndarray:
+    """P(r - delta) for every mode: F^-1[ramp * F P] (§3, first equation)."""
+    h, w = P.shape[-2:]
+    return idft2(shift_ramp(dy, dx_, h, w) * dft2(P))
+
+
+def _patch(O, s, n, h, w):
+    """Object sub-region of slice s under the window at origin n (§2.2: the
+    object is sampled around each probe position to form the transmission
+    functions)."""
+    return O[s, n[0]:n[0] + h, n[1]:n[1] + w]
+
+
+# ------------------------------------------------------- propagator (R3)
+
+def bandlimit_mask(h: int, w: int, beta: float) -> np.ndarray:
+    """Circular anti-alias band limit on the DFT grid (R3)."""
+    if beta <= 0.0:
+        return np.ones((h, w), dtype=bool)
+    x = float(beta) * float(h) * float(w) * 0.5
+    T = math.floor(x * x)
+    fu = freq_index(h).astype(np.int64)[:, None]
+    fv = freq_index(w).astype(np.int64)[None, :]
+    lhs = (fu * w) ** 2 + (fv * h) ** 2
+    return lhs <= T
+
+
+def propagator(h: int, w: int, dx: float, lam: float, dz: float,
+               beta: float) -> np.ndarray:
+    """Band-limited Fresnel propagator over gap dz (§3 and R3)."""
+    qu = freq_index(h)[:, None] / (h * dx)
+    qv = freq_index(w)[None, :] / (w * dx)
+    chirp = np.exp(-1j * np.pi * lam * dz * (qu * qu + qv * qv))
+    return chirp * bandlimit_mask(h, w, beta)
+
+
+def propagate(phi: np.ndarray, Hs: np.ndarray) -> np.ndarray:
+    """Convolution with p(dz) as F^-1[H F phi]."""
+    return idft2(Hs * dft2(phi))
+
+
+# ------------------------------------------------------- forward (§3)
+
+def _check(O, P, pos, g: Geom):
+    O = np.asarray(O, dtype=np.complex128)
+    P = np.asarray(P, dtype=np.complex128)
+    if O.shape != (g.S, g.H, g.W) or P.shape != (g.K, g.h, g.w):
+        raise ValueError("shape mismatch")
+    n, d = split_positions(pos)
+    if (n[:, 0] < 0).any() or (n[:, 1] < 0).any() or \
+       (n[:, 0] + g.h > g.H).any() or (n[:, 1] + g.w > g.W).any():
+        raise ValueError("scan position outside the object")
+    return O, P, n, d
+
+
+def _props(g: Geom):
+    return [propagator(g.h, g.w, g.dx, g.lam, dz, g.bandlimit) for dz in g.dz]
+
+
+def forward_waves(O, P, pos, g: Geom):
+    """Per position: entry waves psi[s] of every slice (K modes each) and the
+    orthonormal far field A of the exit wave.  Returns (psis, A, n, d) with
+    psis [B, S, K, h, w] and A [B, K, h, w]."""
+    O, P, n, d = _check(O, P, pos, g)
+    Hs = _props(g)
+    B = n.shape[0]
+    psis = np.zeros((B, g.S, g.K, g.h, g.w), dtype=np.complex128)
+    A = np.zeros((B, g.K, g.h, g.w), dtype=np.complex128)
+    for j in range(B):
+        psi = shift_probe(P, d[j, 0], d[j, 1])
+        for s in range(g.S):
+            psis[j, s] = psi
+            phi = psi * _patch(O, s, n[j], g.h, g.w)
+            if s < g.S - 1:
+                psi = propagate(phi, Hs[s])
+        A[j] = dft2_ortho(phi)
+    return psis, A, n, d
+
+
+def forward(O, P, pos, g: Geom) -> np.ndarray:
+    """Simulated patterns I [B, h, w] = sum_k |F_o exit_k|^2, DC at [0, 0]."""
+    _, A, _, _ = forward_waves(O, P, pos, g)
+    return np.sum(np.abs(A) ** 2, axis=1)
+
+
+# ----------------------------------------------------------- loss (§3.1)
+
+def loss_terms(I, I_exp, g: Geom):
+    """Per-pixel loss l(I) and its derivative dl/dI (R5)."""
+    I = np.asarray(I, dtype=np.float64)
+    E = np.asarray(I_exp, dtype=np.float64)
+    if g.loss == AMPLITUDE:
+        a = np.sqrt(I + g.c + g.eps)
+        b = np.sqrt(E + g.c + g.eps)
+        return 0.5 * (a - b) ** 2, 0.5 * (1.0 - b / a)
+    if g.loss == POISSON:
+        l = I - E - E * (np.log(I + g.eps) - np.log(E + g.eps))
+        return l, 1.0 - E / (I + g.eps)
+    raise ValueError("unknown loss")
+
+
+def loss_value(I, I_exp, g: Geom) -> float:
+    return float(np.sum(loss_terms(I, I_exp, g)[0]))
+
+
+# ------------------------------------------------------- gradient (§3.2)
+
+def gradient(O, P, pos, I_exp, g: Geom):
+    """Loss and its gradients (R7 convention) with respect to every object
+    slice and every probe mode, by the exact chain rule: for each linear map
+    y = M x the cotangent is M^H g_y; the transmission product gives
+    g_O += conj(psi) g_phi and g_psi = conj(O) g_phi; the seed on the
+    detector is 2 l'(I) A.  Returns (loss, gO [S,H,W], gP [K,h,w])."""
+    psis, A, n, d = forward_waves(O, P, pos, g)
+    O = np.asarray(O, dtype=np.complex128)
+    E = np.asarray(I_exp, dtype=np.float64).reshape(-1, g.h, g.w)
+    Hs = _props(g)
+    gO = np.zeros_like(O)
+    gPhat = np.zeros((g.K, g.h, g.w), dtype=np.complex128)
+    loss = 0.0
+    for j in range(n.shape[0]):
+        I = np.sum(np.abs(A[j]) ** 2, axis=0)
+        l, dl = loss_terms(I, E[j], g)
+        loss += float(np.sum(l))
+        g_phi = idft2_ortho(2.0 * dl * A[j])
+        for s in range(g.S - 1, -1, -1):
+            patch = _patch(O, s, n[j], g.h, g.w)
+            y0, x0 = n[j]
+            gO[s, y0:y0 + g.h, x0:x0 + g.w] += np.sum(np.conj(psis[j, s]) * g_phi, axis=0)
+            g_psi = np.conj(patch) * g_phi
+            if s > 0:
+                g_phi = idft2(np.conj(Hs[s - 1]) * dft2(g_psi))
+        gPhat += np.conj(shift_ramp(d[j, 0], d[j, 1], g.h, g.w)) * dft2(g_psi)
+    gP = idft2(gPhat)
+    return loss, gO, gP
+
+
+def position_gradient(O, P, pos, I_exp, g: Geom) -> np.ndarray:
+    """dL/d(r_y, r_x) per position [B, 2] through the Fourier ramp only (the
+    integer patch origin is piecewise constant).  With psi0 = F^-1[R F P],
+    R = exp(-2 pi i (f_u dy/h + f_v dx/w)): dpsi0/ddy = F^-1[-2 pi i f_u/h R F P],
+    and dL/ddy = Re sum conj(g_psi0) dpsi0/ddy under the R7 convention."""
+    psis, A, n, d = forward_waves(O, P, pos, g)
+    O = np.asarray(O, dtype=np.complex128)
+    P = np.asarray(P, dtype=np.complex128)
+    E = np.asarray(I_exp, dtype=np.float64).reshape(-1, g.h, g.w)
+    Hs = _props(g)
+    FP = dft2(P)
+    fu = freq_index(g.h)[:, None] / g.h
+    fv = freq_index(g.w)[None, :] / g.w
+    out = np.zeros((n.shape[0], 2))
+    for j in range(n.shape[0]):
+        I = np.sum(np.abs(A[j]) ** 2, axis=0)
+        _, dl = loss_terms(I, E[j], g)
+        g_phi = idft2_ortho(2.0 * dl * A[j])
+        for s in range(g.S - 1, -1, -1):
+            g_psi = np.conj(_patch(O, s, n[j], g.h, g.w)) * g_phi
+            if s > 0:
+                g_phi = idft2(np.conj(Hs[s - 1]) * dft2(g_psi))
+        R = shift_ramp(d[j, 0], d[j, 1], g.h, g.w)
+        dpsi_y = idft2(-2j * np.pi * fu * R * FP)
+        dpsi_x = idft2(-2j * np.pi * fv * R * FP)
+        out[j, 0] = float(np.real(np.sum(np.conj(g_psi) * dpsi_y)))
+        out[j, 1] = float(np.real(np.sum(np.conj(g_psi) * dpsi_x)))
+    return out
+
+
+# ----------------------------------------------------------- Adam (§3.2)
+
+def adam_update(z, m, v, gz, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):
+    """One complex Adam step (R8); t counts steps from 1.  Returns new
+    (z, m, v)."""
+    m = b1 * m + (1.0 - b1) * gz
+    v = b2 * v + (1.0 - b2) * (np.abs(gz) ** 2)
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return z - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def step(O, P, mO, vO, mP, vP, t, pos_all, I_exp_all, idx, g: Geom,
+         lr_O, lr_P, b1=0.9, b2=0.999, eps_adam=1e-8, update_probe=True):
+    """One gradient-descent iteration on the minibatch idx (§2.2 grouping,
+    §3.2 solver).  t is the Adam step count AFTER this step.  Returns
+    (O, P, mO, vO, mP, vP, loss, gnorm) where gnorm = sqrt(sum |g|^2) over
+    the object and probe gradients."""
+    idx = np.asarray(idx, dtype=np.int64)
+    pos = np.asarray(pos_all, dtype=np.float64).reshape(-1, 2)[idx]
+    E = np.asarray(I_exp_all, dtype=np.float64).reshape(-1, g.h, g.w)[idx]
+    loss, gO, gP = gradient(O, P, pos, E, g)
+    gnorm = math.sqrt(float(np.sum(np.abs(gO) ** 2) + np.sum(np.abs(gP) ** 2)))
+    O2, mO, vO = adam_update(np.asarray(O, np.complex128), mO, vO, gO, t, lr_O, b1, b2, eps_adam)
+    if update_probe:
+        P2, mP, vP = adam_update(np.asarray(P, np.complex128), mP, vP, gP, t, lr_P, b1, b2, eps_adam)
+    else:
+        P2 = np.asarray(P, np.complex128)
+    return O2, P2, mO, vO, mP, vP, loss, gnorm
