@@ -1,0 +1,265 @@
+/* libptycho: batched mixed-state multislice ptychography forward model and
+ * its adjoint on one NVIDIA B300 (sm_103a).
+ *
+ * The operations follow the problem statement of arXiv 2505.14372 ("phaser"):
+ *   §3    multislice forward model: P_k shifted to each scan position X_j,
+ *         multiplied by each object slice O_i, Fresnel-propagated over the gap
+ *         dz_i under an anti-aliasing band limit, far field
+ *         I = sum_k |F(exit wave_k)|^2 over incoherent probe modes;
+ *   §3.1  amplitude / Anscombe and Poisson noise models (loss per pixel);
+ *   §3.2  gradient of the loss with respect to every object slice and probe
+ *         mode at once, and the Adam solver step;
+ *   §2.2  per-iteration randomised grouping of scan positions;
+ *   §2.3  client/server job model, reduced here to an in-process continuous-
+ *         batching server (ptycho_submit / ptycho_poll).
+ *
+ * Conventions (the paper leaves them open; these are this library's):
+ *   - complex64 is interleaved {re, im} float32 (ptycho_c64);
+ *   - arrays are row-major and contiguous; window h = w = N with
+ *     N in {64, 128, 192, 256}; the object is H x W per slice;
+ *   - a scan position is (y, x) in object pixels of the window's top-left
+ *     corner; the patch origin is floor(r + 1/2), the remainder is applied as
+ *     a Fourier phase ramp (sub-pixel shift P(r - delta));
+ *   - DFT kernel exp(-2 pi i k x / N); the far field is orthonormal; patterns
+ *     have the zero frequency at [0][0] (no fftshift);
+ *   - the Fresnel propagator is exp(-i pi lambda dz |q|^2) times a circular
+ *     band limit at `bandlimit` x Nyquist (<= 0 disables it), applied in each
+ *     of the S-1 propagations;
+ *   - losses are summed over pixels and positions; amplitude/Anscombe:
+ *     1/2 (sqrt(I+c+eps) - sqrt(I_exp+c+eps))^2; Poisson:
+ *     I - I_exp - I_exp (log(I+eps) - log(I_exp+eps));
+ *   - gradients are dL/dRe z + i dL/dIm z (twice the paper's conj(dL/dz)).
+ *
+ * Ownership: every array argument is a DEVICE pointer owned by the caller
+ * unless marked "host".  Calls that take a stream only enqueue work on it
+ * (no synchronisation, no allocation); they are safe to capture in a CUDA
+ * graph.  Calls named *_host copy host buffers in and out and synchronise.
+ *
+ * Errors: every call returns PTYCHO_OK (0) or a negative code; nothing is
+ * thrown across the ABI.  ptycho_last_error() gives a message for the
+ * calling thread.  Arguments are validated on the host before any launch.
+ * Scan positions in device memory are validated by the kernels: an item
+ * whose window leaves the object is skipped and flagged in a device status
+ * word that ptycho_check() reads (it synchronises the stream).
+ */
+#ifndef PTYCHO_H_
+#define PTYCHO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTYCHO_OK 0
+#define PTYCHO_EINVAL (-1)       /* bad dimensions, null pointer, bad option */
+#define PTYCHO_EOUTOFBOUNDS (-2) /* a scan window leaves the object */
+#define PTYCHO_ENOMEM (-3)       /* scratch budget / HBM admission exceeded */
+#define PTYCHO_ECUDA (-4)        /* a CUDA runtime call failed */
+#define PTYCHO_ETIMEDOUT (-5)    /* a bounded wait ran out */
+#define PTYCHO_EBUSY (-6)        /* request not finished / server busy */
+#define PTYCHO_ENOTFOUND (-7)    /* unknown ticket */
+
+typedef struct {
+  float re, im;
+} ptycho_c64;
+
+/* cudaStream_t; NULL is the legacy default stream. */
+typedef void* ptycho_stream;
+
+typedef enum { PTYCHO_LOSS_AMPLITUDE = 0, PTYCHO_LOSS_POISSON = 1 } ptycho_loss;
+
+/* How the adjoint gets the entry wave of every slice: STORE keeps all of
+ * them from the forward pass (B*K*S*N*N*8 bytes of scratch), RECOMPUTE
+ * re-runs the forward inside the adjoint kernel into per-cluster scratch,
+ * AUTO stores when it fits the scratch budget. */
+typedef enum { PTYCHO_WAVES_AUTO = 0, PTYCHO_WAVES_STORE = 1, PTYCHO_WAVES_RECOMPUTE = 2 } ptycho_waves;
+
+/* Geometry and noise model of one reconstruction problem (§3, §3.1). */
+typedef struct {
+  int32_t S, K;       /* slices, incoherent probe modes (K >= 1, S >= 1) */
+  int32_t h, w;       /* window; h == w == N in {64, 128, 192, 256} */
+  int32_t H, W;       /* object slice size, H >= h, W >= w */
+  double dx;          /* pixel size [A] (> 0) */
+  double lambda;      /* electron wavelength [A] (> 0) */
+  const double* dz;   /* host, S-1 slice gaps [A]; copied by ptycho_create */
+  double bandlimit;   /* band limit as a fraction of Nyquist; <= 0: off */
+  int32_t loss;       /* ptycho_loss */
+  double eps;         /* noise-model offset; Poisson needs eps > 0,
+                         amplitude needs eps + c > 0 */
+  double c;           /* amplitude-model offset (0 amplitude, 3/8 Anscombe) */
+  int32_t waves;      /* ptycho_waves */
+} ptycho_geom;
+
+typedef struct ptycho_ctx ptycho_ctx;
+
+/* Creates a context for one geometry on the current CUDA device: builds the
+ * propagator tables and allocates `scratch_budget_bytes` of device scratch
+ * once (0 picks the size that one call with B = max_batch needs).
+ * max_batch bounds B in every later call.  Returns EINVAL / ENOMEM / ECUDA. */
+int ptycho_create(const ptycho_geom* geom, int32_t max_batch, size_t scratch_budget_bytes,
+                  ptycho_ctx** out);
+int ptycho_destroy(ptycho_ctx* ctx);
+
+/* Bytes of scratch one forward+adjoint call with B positions needs under
+ * the given waves mode (STORE or RECOMPUTE; AUTO reports STORE). */
+size_t ptycho_scratch_bytes(const ptycho_geom* geom, int32_t B, int32_t waves);
+
+/* Forward model (§3): I_out[B][N][N] (float32, zero frequency at [0][0]) =
+ * sum_k |F_o psi_exit(j, k)|^2 for the B positions pos[B][2].
+ * O: [S][H][W], P: [K][N][N] complex64. */
+int ptycho_forward(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
+                   int32_t B, float* I_out, ptycho_stream stream);
+
+/* Loss and gradient (§3.1, §3.2) for B positions with measured patterns
+ * I_exp[B][N][N].  loss_out: device double (may be NULL).  gO [S][H][W] and
+ * gP [K][N][N] are overwritten, or added to when accumulate != 0. */
+int ptycho_adjoint(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
+                   int32_t B, const float* I_exp, double* loss_out, ptycho_c64* gO, ptycho_c64* gP,
+                   int32_t accumulate, ptycho_stream stream);
+
+/* Vector-Jacobian product of the forward model (§3.2: the gradient engine
+ * of the paper is the VJP of the forward simulation): for a cotangent
+ * gI[B][N][N] = dL/dI of any real loss L(I), writes (or adds, accumulate
+ * != 0) gO = dL/dRe O + i dL/dIm O and gP likewise.  The entry waves are
+ * recomputed from O, P and pos (nothing is kept from ptycho_forward). */
+int ptycho_vjp(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
+               const float* gI, ptycho_c64* gO, ptycho_c64* gP, int32_t accumulate, ptycho_stream stream);
+
+/* Adam hyper-parameters (§3.2; Optax-style defaults 0.9, 0.999, 1e-8). */
+typedef struct {
+  float lr_O, lr_P;
+  float beta1, beta2, eps;
+  int32_t update_probe; /* 0: the probe is held fixed */
+} ptycho_opt;
+
+/* Adam state: first moments m (complex64), second moments v (float32, |g|^2
+ * based), device arrays shaped like O and P; t = steps taken (host, updated
+ * by ptycho_step). */
+typedef struct {
+  ptycho_c64* mO;
+  float* vO;
+  ptycho_c64* mP;
+  float* vP;
+  int64_t t;
+} ptycho_adam;
+
+/* One gradient-descent iteration on one group of B scan positions:
+ * idx[B] (device int32, each in [0, n_pos)) selects positions
+ * pos_all[n_pos][2] and patterns I_exp_all[n_pos][N][N]; an index outside
+ * that range is skipped and flagged like an out-of-bounds window; loss and gradient as ptycho_adjoint, then Adam on O
+ * (and P unless update_probe == 0), in place.  stats_out (device double[2],
+ * may be NULL) receives {loss, sqrt(sum |gO|^2 + sum |gP|^2)}. */
+int ptycho_step(ptycho_ctx* ctx, ptycho_c64* O, ptycho_c64* P, ptycho_adam* state,
+                const ptycho_opt* opt, const float* pos_all, const float* I_exp_all, int32_t n_pos,
+                const int32_t* idx, int32_t B, double* stats_out, ptycho_stream stream);
+
+/* ptycho_step with the group's positions and patterns in HOST memory
+ * (pinned memory gives the fastest copies): copies them to the device,
+ * steps, and returns loss and gradient norm to host doubles.  Synchronises
+ * the stream.  Positions are validated on the host (EOUTOFBOUNDS). */
+int ptycho_step_host(ptycho_ctx* ctx, ptycho_c64* O, ptycho_c64* P, ptycho_adam* state,
+                     const ptycho_opt* opt, const float* pos_host, const float* I_exp_host,
+                     int32_t B, double* loss_host, double* gnorm_host, ptycho_stream stream);
+
+/* Synchronises `stream` and reports (then clears) the device status word:
+ * PTYCHO_EOUTOFBOUNDS if any item was skipped since the last check. */
+int ptycho_check(ptycho_ctx* ctx, ptycho_stream stream);
+
+/* Grouping (§2.2): writes a permutation of 0..P-1 into out_idx[P] (host)
+ * for `iteration` of a run seeded by `seed`; consecutive runs of B indices
+ * are the groups.  mode 0 = sparse (random groups), 1 = compact (spatially
+ * contiguous groups from a raster ordering of pos_host[P][2], group order
+ * shuffled).  Deterministic across platforms. */
+int ptycho_make_groups(int32_t P, int32_t B, uint64_t seed, int64_t iteration, int32_t mode,
+                       const float* pos_host, int32_t* out_idx);
+
+/* Per-kernel device time accumulated by this context's launches since the
+ * last reset (CUDA events on the launching stream), enabled with
+ * ptycho_set_timing(ctx, 1).  names/ms are host arrays of length cap;
+ * returns the number of entries, or a negative code. */
+int ptycho_set_timing(ptycho_ctx* ctx, int32_t enable);
+int ptycho_kernel_times(ptycho_ctx* ctx, const char** names, double* ms, int32_t* launches, int32_t cap);
+
+/* Stand-alone 2-D DFT of `count` natural-order N x N complex64 arrays
+ * through the same shared-memory tile the model uses (dir < 0 forward,
+ * dir > 0 inverse, both unnormalised).  For tests and diagnostics. */
+int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count,
+                ptycho_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving (§2.3 job model, in process): requests from datasets of different
+ * shapes are admitted against an HBM budget, keep their object, probe and
+ * Adam state resident on the device, and have their iterations batched into
+ * shared launches with the other admitted requests.  All request data is
+ * host memory; results point into library-owned host buffers that stay
+ * valid until ptycho_release. */
+typedef struct ptycho_server ptycho_server;
+
+typedef struct {
+  ptycho_geom geom;          /* geom.dz must stay valid until submit returns */
+  int32_t n_pos;             /* scan positions P */
+  const float* pos;          /* host [P][2] */
+  const float* I_exp;        /* host [P][N][N] */
+  const ptycho_c64* O_init;  /* host [S][H][W], or NULL for vacuum (O = 1) */
+  const ptycho_c64* P_init;  /* host [K][N][N] */
+  int32_t iterations;        /* full passes over the P positions */
+  int32_t batch;             /* group size B */
+  int32_t grouping;          /* 0 sparse, 1 compact */
+  uint64_t seed;
+  ptycho_opt opt;
+} ptycho_request;
+
+#define PTYCHO_REQ_QUEUED 0
+#define PTYCHO_REQ_RUNNING 1
+#define PTYCHO_REQ_DONE 2
+#define PTYCHO_REQ_FAILED 3
+
+typedef struct {
+  int32_t state;               /* PTYCHO_REQ_* */
+  int32_t iterations_done;
+  int32_t error;               /* error code when FAILED */
+  double last_loss;
+  double submit_ms, start_ms, finish_ms; /* wall clock relative to server start */
+} ptycho_status;
+
+typedef struct {
+  const ptycho_c64* O;         /* host [S][H][W] (valid until release) */
+  const ptycho_c64* P;         /* host [K][N][N] */
+  const double* loss;          /* host [iterations * groups] per-step losses */
+  int32_t n_loss;
+  const double* step_ms;       /* host, device time of every shared launch this request rode in */
+  int32_t n_step;
+} ptycho_result;
+
+typedef struct {
+  int64_t submitted, admitted, finished, failed;
+  int64_t queue_depth;
+  size_t admitted_bytes, budget_bytes;
+  int64_t launches;            /* shared forward/adjoint launches issued */
+  double positions_per_s;      /* over the server's busy time */
+  double p50_iter_ms, p99_iter_ms; /* per-iteration latency over finished steps */
+} ptycho_server_stats;
+
+/* hbm_budget_bytes: device memory the server may hold for admitted
+ * requests (state + scratch).  max_active: requests resident at once. */
+int ptycho_server_create(size_t hbm_budget_bytes, int32_t max_active, ptycho_server** out);
+int ptycho_server_destroy(ptycho_server* srv); /* cancels unfinished work */
+/* Non-blocking; copies the request's host arrays.  ENOMEM if the request
+ * alone exceeds the budget. */
+int ptycho_submit(ptycho_server* srv, const ptycho_request* req, uint64_t* ticket);
+/* Non-blocking; fills st (and res once DONE).  ENOTFOUND for unknown tickets. */
+int ptycho_poll(ptycho_server* srv, uint64_t ticket, ptycho_status* st, ptycho_result* res);
+/* Blocks until the ticket is DONE/FAILED or timeout_ms passes (ETIMEDOUT). */
+int ptycho_wait(ptycho_server* srv, uint64_t ticket, double timeout_ms);
+int ptycho_release(ptycho_server* srv, uint64_t ticket);
+int ptycho_server_stats_get(ptycho_server* srv, ptycho_server_stats* out);
+
+const char* ptycho_last_error(void);
+const char* ptycho_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTYCHO_H_ */

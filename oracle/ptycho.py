@@ -65,7 +65,7 @@ __all__ = [
     "idft2", "dft2_ortho", "idft2_ortho", "split_positions", "shift_ramp",
     "shift_probe", "bandlimit_mask", "propagator", "propagate",
     "forward", "forward_waves", "loss_terms", "loss_value", "gradient",
-    "adam_update", "step", "position_gradient",
+    "adam_update", "step", "position_gradient", "vjp",
 ]
 
 
@@ -260,24 +260,16 @@ def loss_value(I, I_exp, g: Geom) -> float:
 
 # ------------------------------------------------------- gradient (§3.2)
 
-def gradient(O, P, pos, I_exp, g: Geom):
-    """Loss and its gradients (R7 convention) with respect to every object
-    slice and every probe mode, by the exact chain rule: for each linear map
-    y = M x the cotangent is M^H g_y; the transmission product gives
-    g_O += conj(psi) g_phi and g_psi = conj(O) g_phi; the seed on the
-    detector is 2 l'(I) A.  Returns (loss, gO [S,H,W], gP [K,h,w])."""
-    psis, A, n, d = forward_waves(O, P, pos, g)
-    O = np.asarray(O, dtype=np.complex128)
-    E = np.asarray(I_exp, dtype=np.float64).reshape(-1, g.h, g.w)
+def _backprop(O, psis, A, n, d, seeds, g: Geom):
+    """Cotangents of O and P from detector-plane seeds g_A [B, K, h, w]
+    (R7 convention) by the exact chain rule: for each linear map y = M x the
+    cotangent is M^H g_y; the transmission product gives
+    g_O += conj(psi) g_phi and g_psi = conj(O) g_phi."""
     Hs = _props(g)
     gO = np.zeros_like(O)
     gPhat = np.zeros((g.K, g.h, g.w), dtype=np.complex128)
-    loss = 0.0
     for j in range(n.shape[0]):
-        I = np.sum(np.abs(A[j]) ** 2, axis=0)
-        l, dl = loss_terms(I, E[j], g)
-        loss += float(np.sum(l))
-        g_phi = idft2_ortho(2.0 * dl * A[j])
+        g_phi = idft2_ortho(seeds[j])
         for s in range(g.S - 1, -1, -1):
             patch = _patch(O, s, n[j], g.h, g.w)
             y0, x0 = n[j]
@@ -286,8 +278,34 @@ def gradient(O, P, pos, I_exp, g: Geom):
             if s > 0:
                 g_phi = idft2(np.conj(Hs[s - 1]) * dft2(g_psi))
         gPhat += np.conj(shift_ramp(d[j, 0], d[j, 1], g.h, g.w)) * dft2(g_psi)
-    gP = idft2(gPhat)
+    return gO, idft2(gPhat)
+
+
+def gradient(O, P, pos, I_exp, g: Geom):
+    """Loss and its gradients (R7 convention) with respect to every object
+    slice and every probe mode; the detector seed is 2 l'(I) A.
+    Returns (loss, gO [S,H,W], gP [K,h,w])."""
+    psis, A, n, d = forward_waves(O, P, pos, g)
+    O = np.asarray(O, dtype=np.complex128)
+    E = np.asarray(I_exp, dtype=np.float64).reshape(-1, g.h, g.w)
+    seeds = np.zeros_like(A)
+    loss = 0.0
+    for j in range(n.shape[0]):
+        I = np.sum(np.abs(A[j]) ** 2, axis=0)
+        l, dl = loss_terms(I, E[j], g)
+        loss += float(np.sum(l))
+        seeds[j] = 2.0 * dl * A[j]
+    gO, gP = _backprop(O, psis, A, n, d, seeds, g)
     return loss, gO, gP
+
+
+def vjp(O, P, pos, gI, g: Geom):
+    """Vector-Jacobian product of the forward model for a cotangent
+    gI = dL/dI [B, h, w]: seed 2 gI A.  Returns (gO, gP)."""
+    psis, A, n, d = forward_waves(O, P, pos, g)
+    O = np.asarray(O, dtype=np.complex128)
+    G = np.asarray(gI, dtype=np.float64).reshape(-1, 1, g.h, g.w)
+    return _backprop(O, psis, A, n, d, 2.0 * G * A, g)
 
 
 def position_gradient(O, P, pos, I_exp, g: Geom) -> np.ndarray:

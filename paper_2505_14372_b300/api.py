@@ -1,0 +1,228 @@
+"""Python binding of libptycho with torch tensors as device memory.
+
+Each method checks shapes, dtypes and devices, passes raw pointers and the
+current torch stream to the C-ABI, and raises PtychoError on failure.  All
+arithmetic happens in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+LOSS = {"amplitude": 0, "anscombe": 0, "poisson": 1}
+WAVES = {"auto": 0, "store": 1, "recompute": 2}
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _need(t: torch.Tensor, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+
+
+@dataclass
+class Geometry:
+    S: int
+    K: int
+    N: int
+    H: int
+    W: int
+    dx: float = 0.1
+    lam: float = 0.0197
+    dz: tuple = ()
+    bandlimit: float = 2.0 / 3.0
+    loss: str = "amplitude"
+    eps: float = 1e-3
+    c: float = 0.0
+    waves: str = "auto"
+
+    def to_c(self):
+        dz = (C.c_double * max(len(self.dz), 1))(*self.dz) if len(self.dz) else None
+        g = _lib.Geom(self.S, self.K, self.N, self.N, self.H, self.W, self.dx, self.lam,
+                      C.cast(dz, C.POINTER(C.c_double)) if dz is not None else None,
+                      self.bandlimit, LOSS[self.loss], self.eps, self.c, WAVES[self.waves])
+        return g, dz
+
+
+def adam_opt(lr_O=1e-3, lr_P=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, update_probe=True) -> _lib.Opt:
+    return _lib.Opt(lr_O, lr_P, beta1, beta2, eps, 1 if update_probe else 0)
+
+
+class AdamState:
+    """First/second moments for O and P on the device, step counter t."""
+
+    def __init__(self, geom: Geometry, device="cuda"):
+        self.mO = torch.zeros((geom.S, geom.H, geom.W), dtype=torch.complex64, device=device)
+        self.vO = torch.zeros((geom.S, geom.H, geom.W), dtype=torch.float32, device=device)
+        self.mP = torch.zeros((geom.K, geom.N, geom.N), dtype=torch.complex64, device=device)
+        self.vP = torch.zeros((geom.K, geom.N, geom.N), dtype=torch.float32, device=device)
+        self.c = _lib.Adam(self.mO.data_ptr(), self.vO.data_ptr(), self.mP.data_ptr(), self.vP.data_ptr(), 0)
+
+    @property
+    def t(self) -> int:
+        return int(self.c.t)
+
+
+class Context:
+    """One problem geometry on the current CUDA device (ptycho_create)."""
+
+    def __init__(self, geom: Geometry, max_batch: int, scratch_budget: int = 0):
+        self.geom = geom
+        self.max_batch = int(max_batch)
+        g, self._dz = geom.to_c()
+        h = C.c_void_p()
+        check(lib().ptycho_create(C.byref(g), self.max_batch, scratch_budget, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().ptycho_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- shapes
+    def _oshape(self):
+        g = self.geom
+        return (g.S, g.H, g.W)
+
+    def _pshape(self):
+        g = self.geom
+        return (g.K, g.N, g.N)
+
+    def forward(self, O, P, pos, out=None) -> torch.Tensor:
+        g = self.geom
+        B = pos.shape[0]
+        _need(O, torch.complex64, self._oshape(), "O")
+        _need(P, torch.complex64, self._pshape(), "P")
+        _need(pos, torch.float32, (B, 2), "pos")
+        if out is None:
+            out = torch.empty((B, g.N, g.N), dtype=torch.float32, device=O.device)
+        check(lib().ptycho_forward(self.h, _ptr(O), _ptr(P), _ptr(pos), B, _ptr(out), _stream()))
+        return out
+
+    def adjoint(self, O, P, pos, I_exp, gO=None, gP=None, accumulate=False):
+        """Returns (loss [device float64 scalar tensor], gO, gP)."""
+        B = pos.shape[0]
+        g = self.geom
+        _need(O, torch.complex64, self._oshape(), "O")
+        _need(P, torch.complex64, self._pshape(), "P")
+        _need(pos, torch.float32, (B, 2), "pos")
+        _need(I_exp, torch.float32, (B, g.N, g.N), "I_exp")
+        if gO is None:
+            gO = torch.empty_like(O)
+        if gP is None:
+            gP = torch.empty_like(P)
+        loss = torch.zeros((), dtype=torch.float64, device=O.device)
+        check(lib().ptycho_adjoint(self.h, _ptr(O), _ptr(P), _ptr(pos), B, _ptr(I_exp), _ptr(loss),
+                                   _ptr(gO), _ptr(gP), 1 if accumulate else 0, _stream()))
+        return loss, gO, gP
+
+    def vjp(self, O, P, pos, gI, gO=None, gP=None, accumulate=False):
+        B = pos.shape[0]
+        g = self.geom
+        _need(gI, torch.float32, (B, g.N, g.N), "gI")
+        if gO is None:
+            gO = torch.empty_like(O)
+        if gP is None:
+            gP = torch.empty_like(P)
+        check(lib().ptycho_vjp(self.h, _ptr(O), _ptr(P), _ptr(pos), B, _ptr(gI), _ptr(gO), _ptr(gP),
+                               1 if accumulate else 0, _stream()))
+        return gO, gP
+
+    def step(self, O, P, state: AdamState, opt, pos_all, I_exp_all, idx, stats=None):
+        """One Adam iteration on the minibatch idx (int32 device tensor);
+        returns a device float64 tensor [loss, grad-norm]."""
+        B = idx.shape[0]
+        _need(idx, torch.int32, (B,), "idx")
+        if stats is None:
+            stats = torch.zeros(2, dtype=torch.float64, device=O.device)
+        g = self.geom
+        n_pos = pos_all.shape[0]
+        _need(pos_all, torch.float32, (n_pos, 2), "pos_all")
+        _need(I_exp_all, torch.float32, (n_pos, g.N, g.N), "I_exp_all")
+        check(lib().ptycho_step(self.h, _ptr(O), _ptr(P), C.byref(state.c), C.byref(opt), _ptr(pos_all),
+                                _ptr(I_exp_all), n_pos, _ptr(idx), B, _ptr(stats), _stream()))
+        return stats
+
+    def step_host(self, O, P, state: AdamState, opt, pos_host: np.ndarray, I_exp_host):
+        """Step with the group's positions/patterns in host memory (numpy or
+        pinned CPU torch tensors); returns (loss, gnorm) as floats."""
+        if isinstance(pos_host, torch.Tensor):
+            B = pos_host.shape[0]
+            pp, ip = pos_host.data_ptr(), I_exp_host.data_ptr()
+        else:
+            pos_host = np.ascontiguousarray(pos_host, dtype=np.float32)
+            I_exp_host = np.ascontiguousarray(I_exp_host, dtype=np.float32)
+            B = pos_host.shape[0]
+            pp, ip = pos_host.ctypes.data, I_exp_host.ctypes.data
+        loss = C.c_double()
+        gn = C.c_double()
+        check(lib().ptycho_step_host(self.h, _ptr(O), _ptr(P), C.byref(state.c), C.byref(opt), pp, ip, B,
+                                     C.byref(loss), C.byref(gn), _stream()))
+        return loss.value, gn.value
+
+    def check_status(self):
+        check(lib().ptycho_check(self.h, _stream()))
+
+    def set_timing(self, on=True):
+        check(lib().ptycho_set_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self, reset=False) -> dict:
+        cap = 64
+        names = (C.c_char_p * cap)()
+        ms = (C.c_double * cap)()
+        n_l = (C.c_int32 * cap)()
+        n = lib().ptycho_kernel_times(self.h, names, ms, n_l, cap)
+        if n < 0:
+            check(n)
+        out = {names[i].decode(): (ms[i], n_l[i]) for i in range(min(n, cap))}
+        if reset:
+            lib().ptycho_kernel_times(self.h, None, None, None, -1)
+        return out
+
+
+def scratch_bytes(geom: Geometry, B: int, waves: str = "store") -> int:
+    g, _dz = geom.to_c()
+    return int(lib().ptycho_scratch_bytes(C.byref(g), B, WAVES[waves]))
+
+
+def fft2(x: torch.Tensor, inverse=False) -> torch.Tensor:
+    """Unnormalised 2-D DFT of [count, N, N] complex64 through the tile."""
+    assert x.dtype == torch.complex64 and x.is_cuda and x.is_contiguous() and x.dim() == 3
+    out = torch.empty_like(x)
+    check(lib().ptycho_fft2(x.shape[-1], 1 if inverse else -1, _ptr(x), _ptr(out), x.shape[0], _stream()))
+    return out
+
+
+def make_groups(P: int, B: int, seed: int, iteration: int, mode: str = "sparse", pos=None) -> np.ndarray:
+    out = np.empty(P, dtype=np.int32)
+    pp = None
+    if pos is not None:
+        pos = np.ascontiguousarray(pos, dtype=np.float32)
+        pp = pos.ctypes.data
+    check(lib().ptycho_make_groups(P, B, seed, iteration, {"sparse": 0, "compact": 1}[mode], pp,
+                                   out.ctypes.data))
+    return out
+
+
+def version() -> str:
+    return lib().ptycho_version().decode()

@@ -1,0 +1,562 @@
+// C-ABI of libptycho: contexts, validation, scratch arena, launch sequences
+// of the forward model, the adjoint and the gradient-descent step
+// (arXiv 2505.14372 §3, §3.1, §3.2), grouping (§2.2) and kernel timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "errors.h"
+#include "ptycho.h"
+
+using ptycho::EngineOps;
+using ptycho::LaunchArgs;
+using ptycho::ProblemDesc;
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Offsets of one call's scratch inside the context arena.
+struct Layout {
+  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, waves, total;
+};
+
+Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
+  const size_t NP = (size_t)g.h * g.w;
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  L.Phat = take((size_t)g.K * NP * 8);
+  L.A = take((size_t)B * g.K * NP * 8);
+  L.w = take((size_t)B * NP * 4);
+  L.gPhat = take((size_t)g.K * NP * 8);
+  L.partials = take((size_t)(ptycho::kLossBlocks + 2 * ptycho::kNormBlocks + 8) * 8);
+  L.stats = take(4 * 8);
+  L.stage_pos = take((size_t)B * 2 * 4);
+  L.stage_I = take((size_t)B * NP * 4);
+  L.waves = take(store ? (size_t)B * g.K * g.S * NP * 8 : (size_t)slots * g.S * NP * 8);
+  L.total = off;
+  return L;
+}
+
+int validate_geom(const ptycho_geom* g) {
+  if (!g) return perr(PTYCHO_EINVAL, "geometry is NULL");
+  if (g->S < 1 || g->K < 1) return perr(PTYCHO_EINVAL, "need S >= 1 and K >= 1");
+  if (g->h != g->w) return perr(PTYCHO_EINVAL, "window must be square (h == w)");
+  if (!ptycho::engine_for(g->h))
+    return perr(PTYCHO_EINVAL, "window size " + std::to_string(g->h) + " not in {64, 128, 192, 256}");
+  if (g->H < g->h || g->W < g->w) return perr(PTYCHO_EINVAL, "object smaller than the window");
+  if (!(g->dx > 0) || !(g->lambda > 0) || !std::isfinite(g->dx) || !std::isfinite(g->lambda))
+    return perr(PTYCHO_EINVAL, "dx and lambda must be finite and > 0");
+  if (g->S > 1 && !g->dz) return perr(PTYCHO_EINVAL, "dz is NULL but S > 1");
+  for (int i = 0; i + 1 < g->S; ++i)
+    if (!std::isfinite(g->dz[i])) return perr(PTYCHO_EINVAL, "dz must be finite");
+  if (!std::isfinite(g->bandlimit)) return perr(PTYCHO_EINVAL, "bandlimit must be finite");
+  if (g->loss != PTYCHO_LOSS_AMPLITUDE && g->loss != PTYCHO_LOSS_POISSON)
+    return perr(PTYCHO_EINVAL, "unknown loss");
+  if (!(g->eps >= 0) || !(g->c >= 0)) return perr(PTYCHO_EINVAL, "eps and c must be >= 0");
+  if (g->loss == PTYCHO_LOSS_POISSON && !(g->eps > 0)) return perr(PTYCHO_EINVAL, "Poisson loss needs eps > 0");
+  if (g->loss == PTYCHO_LOSS_AMPLITUDE && !(g->eps + g->c > 0))
+    return perr(PTYCHO_EINVAL, "amplitude loss needs eps + c > 0");
+  if (g->waves < 0 || g->waves > 2) return perr(PTYCHO_EINVAL, "unknown waves mode");
+  const double cells = (double)g->S * g->H * g->W;
+  if (cells > 4.0e9) return perr(PTYCHO_EINVAL, "object too large");
+  return PTYCHO_OK;
+}
+
+// Band-limit threshold on f_u^2 + f_v^2 (square window): the grid keeps
+// (f_u w)^2 + (f_v h)^2 <= floor(x*x) with x = beta*h*w*0.5 in IEEE double.
+int band_threshold(const ptycho_geom& g) {
+  if (!(g.bandlimit > 0)) return -1;
+  const double x = g.bandlimit * (double)g.h * (double)g.w * 0.5;
+  const double T = std::floor(x * x);
+  const double NN = (double)g.h * (double)g.h;
+  const double q = std::floor(T / NN);
+  return (int)std::min(q, 2.0e9);
+}
+
+}  // namespace
+
+struct ptycho_ctx {
+  ptycho_geom g{};
+  std::vector<double> dz;
+  const EngineOps* ops = nullptr;
+  int N = 0, NP = 0, max_batch = 0, device = 0;
+  float2* Hc = nullptr;
+  int blT = -1;
+  unsigned* status = nullptr;
+  float2* gO = nullptr;
+  float2* gP = nullptr;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool store = true;
+  int slots = 0;          // recompute slots (clusters of the recompute adjoint)
+  int res_fwd = 1, res_adj = 1;
+  // timing
+  bool timing = false;
+  struct Pending {
+    int kid;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::string> names;
+  std::vector<double> ms;
+  std::vector<int> launches;
+};
+
+namespace {
+
+int kernel_id(ptycho_ctx* c, const char* name) {
+  for (size_t i = 0; i < c->names.size(); ++i)
+    if (c->names[i] == name) return (int)i;
+  c->names.emplace_back(name);
+  c->ms.push_back(0.0);
+  c->launches.push_back(0);
+  return (int)c->names.size() - 1;
+}
+
+cudaEvent_t take_event(ptycho_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one launch with CUDA events on its stream when timing is on.
+struct Timed {
+  ptycho_ctx* c;
+  cudaStream_t s;
+  int kid = -1;
+  cudaEvent_t a = nullptr;
+  Timed(ptycho_ctx* ctx, const char* name, cudaStream_t st) : c(ctx), s(st) {
+    if (!c->timing) return;
+    kid = kernel_id(c, name);
+    a = take_event(c);
+    cudaEventRecord(a, s);
+  }
+  ~Timed() {
+    if (kid < 0) return;
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, s);
+    c->pending.push_back({kid, a, b});
+  }
+};
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return perr(PTYCHO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+ProblemDesc base_desc(ptycho_ctx* c, const Layout& L, const ptycho_c64* O, const float* pos, const int* idx,
+                      int B, int npos) {
+  ProblemDesc d{};
+  d.O = reinterpret_cast<const float2*>(O);
+  d.Phat = reinterpret_cast<const float2*>(c->arena + L.Phat);
+  d.pos = pos;
+  d.idx = idx;
+  d.Hc = c->Hc;
+  d.A = reinterpret_cast<float2*>(c->arena + L.A);
+  d.w = reinterpret_cast<const float*>(c->arena + L.w);
+  d.waves = c->store ? reinterpret_cast<float2*>(c->arena + L.waves) : nullptr;
+  d.gO = nullptr;
+  d.gPhat = reinterpret_cast<float2*>(c->arena + L.gPhat);
+  d.S = c->g.S;
+  d.K = c->g.K;
+  d.H = c->g.H;
+  d.W = c->g.W;
+  d.B = B;
+  d.npos = npos;
+  d.blT = c->blT;
+  d.item0 = 0;
+  return d;
+}
+
+LaunchArgs one_problem(ptycho_ctx* c, const Layout& L, const ProblemDesc& d) {
+  LaunchArgs a{};
+  a.d[0] = d;
+  a.nd = 1;
+  a.total = d.B * d.K;
+  a.status = c->status;
+  a.slots = reinterpret_cast<float2*>(c->arena + L.waves);
+  a.slot_stride = (long long)c->g.S * c->NP;
+  return a;
+}
+
+int check_call(ptycho_ctx* c, int B) {
+  if (!c) return perr(PTYCHO_EINVAL, "context is NULL");
+  if (B < 0 || B > c->max_batch)
+    return perr(PTYCHO_EINVAL, "B = " + std::to_string(B) + " outside [0, max_batch = " + std::to_string(c->max_batch) + "]");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) {
+    cudaGetLastError();
+    return perr(PTYCHO_EINVAL, "current CUDA device differs from the context's device");
+  }
+  return PTYCHO_OK;
+}
+
+// forward + loss + adjoint into (gO, gP); partials[0..nl) hold the loss.
+// With gI != null the seed is the external cotangent dL/dI instead of the
+// noise model's derivative (vector-Jacobian product).
+int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, const int* idx, int B,
+                 int npos, const float* Iexp, ptycho_c64* gO, ptycho_c64* gP, int accumulate, cudaStream_t s, int* nl_out,
+                 bool vjp = false, const float* gI = nullptr) {
+  const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
+  const int K = c->g.K;
+  float2* Phat = reinterpret_cast<float2*>(c->arena + L.Phat);
+  float2* gPhat = reinterpret_cast<float2*>(c->arena + L.gPhat);
+  double* partials = reinterpret_cast<double*>(c->arena + L.partials);
+  const long long nO = (long long)c->g.S * c->g.H * c->g.W;
+  {
+    Timed t(c, "probe_spectrum", s);
+    CK(c->ops->probe_spectrum(reinterpret_cast<const float2*>(P), Phat, K, s));
+  }
+  CK(cudaMemsetAsync(gPhat, 0, (size_t)K * c->NP * 8, s));
+  if (!accumulate) CK(cudaMemsetAsync(gO, 0, (size_t)nO * 8, s));
+  const int nl = (int)std::min<long long>(ptycho::kLossBlocks, std::max<long long>(1, ((long long)B * c->NP + 255) / 256));
+  *nl_out = nl;
+  if (B == 0) {
+    CK(cudaMemsetAsync(partials, 0, (size_t)nl * 8, s));
+    if (!accumulate) CK(cudaMemsetAsync(gP, 0, (size_t)K * c->NP * 8, s));
+    return PTYCHO_OK;
+  }
+  ProblemDesc d = base_desc(c, L, O, pos, idx, B, npos);
+  d.gO = reinterpret_cast<float2*>(gO);
+  LaunchArgs la = one_problem(c, L, d);
+  const int items = B * K;
+  {
+    Timed t(c, "forward", s);
+    CK(c->ops->forward(la, std::min(items, c->res_fwd), c->store, s));
+  }
+  if (vjp) {
+    Timed t(c, "seed", s);
+    CK(c->ops->seed(gI, B, reinterpret_cast<float*>(c->arena + L.w), s));
+  } else {
+    Timed t(c, "loss", s);
+    CK(c->ops->loss(d.A, Iexp, idx, npos, B, K, c->g.loss, (float)c->g.eps, (float)c->g.c,
+                    reinterpret_cast<float*>(c->arena + L.w), partials, nl, s));
+  }
+  {
+    Timed t(c, "adjoint", s);
+    const int cl = c->store ? std::min(items, c->res_adj) : std::min(items, c->slots);
+    CK(c->ops->adjoint(la, cl, c->store, s));
+  }
+  {
+    Timed t(c, "probe_grad", s);
+    CK(c->ops->probe_grad(gPhat, reinterpret_cast<float2*>(gP), K, accumulate, s));
+  }
+  return PTYCHO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ptycho_create(const ptycho_geom* geom, int32_t max_batch, size_t scratch_budget_bytes, ptycho_ctx** out) {
+  if (!out) return perr(PTYCHO_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_geom(geom);
+  if (rc) return rc;
+  if (max_batch < 1) return perr(PTYCHO_EINVAL, "max_batch must be >= 1");
+  if ((long long)max_batch * geom->K >= (1LL << 31)) return perr(PTYCHO_EINVAL, "max_batch * K too large");
+  auto* c = new ptycho_ctx();
+  c->g = *geom;
+  c->dz.assign(geom->dz ? geom->dz : nullptr, geom->dz ? geom->dz + std::max(geom->S - 1, 0) : nullptr);
+  c->g.dz = c->dz.data();
+  c->ops = ptycho::engine_for(geom->h);
+  c->N = geom->h;
+  c->NP = geom->h * geom->w;
+  c->max_batch = max_batch;
+  c->blT = band_threshold(*geom);
+  auto bail = [&](int code) {
+    ptycho_destroy(c);
+    return code;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return perr(PTYCHO_ECUDA, "no CUDA device");
+  }
+  c->res_fwd = c->ops->resident_clusters(false, false);
+  c->slots = c->ops->resident_clusters(true, false);
+  c->res_adj = c->ops->resident_clusters(true, true);
+  // waves mode
+  const Layout Ls = make_layout(c->g, max_batch, true, 0);
+  const Layout Lr = make_layout(c->g, max_batch, false, c->slots);
+  if (geom->waves == PTYCHO_WAVES_STORE) c->store = true;
+  else if (geom->waves == PTYCHO_WAVES_RECOMPUTE) c->store = false;
+  else c->store = scratch_budget_bytes == 0 || Ls.total <= scratch_budget_bytes;
+  const Layout& L = c->store ? Ls : Lr;
+  if (scratch_budget_bytes && L.total > scratch_budget_bytes)
+    return bail(perr(PTYCHO_ENOMEM, "scratch needs " + std::to_string(L.total) + " bytes, budget is " +
+                                        std::to_string(scratch_budget_bytes)));
+  c->arena_bytes = L.total;
+  if (cudaMalloc(&c->arena, c->arena_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->arena = nullptr;
+    return bail(perr(PTYCHO_ENOMEM, "cudaMalloc of " + std::to_string(c->arena_bytes) + " scratch bytes failed"));
+  }
+  const size_t nO = (size_t)geom->S * geom->H * geom->W;
+  if (cudaMalloc(&c->gO, nO * 8) != cudaSuccess || cudaMalloc(&c->gP, (size_t)geom->K * c->NP * 8) != cudaSuccess ||
+      cudaMalloc(&c->status, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(perr(PTYCHO_ENOMEM, "cudaMalloc of gradient buffers failed"));
+  }
+  if (cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) return bail(perr(PTYCHO_ECUDA, "memset"));
+  // separable Fresnel chirp per gap, in spectral slot order (FP64 phase in turns, reduced)
+  if (geom->S > 1) {
+    std::vector<float2> h((size_t)(geom->S - 1) * c->N);
+    const int R1 = c->ops->R1, R2 = c->ops->R2, N = c->N;
+    for (int s = 0; s + 1 < geom->S; ++s)
+      for (int p = 0; p < N; ++p) {
+        const int n = p / R2 + R1 * (p % R2);
+        const double f = n < (N + 1) / 2 ? n : n - N;
+        double t = geom->lambda * c->dz[s] * f * f / (2.0 * (double)N * N * geom->dx * geom->dx);
+        t -= std::nearbyint(t);
+        const double a = -2.0 * M_PI * t;
+        h[(size_t)s * N + p] = make_float2((float)std::cos(a), (float)std::sin(a));
+      }
+    if (cudaMalloc(&c->Hc, h.size() * sizeof(float2)) != cudaSuccess ||
+        cudaMemcpy(c->Hc, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(perr(PTYCHO_ENOMEM, "propagator table allocation failed"));
+    }
+  }
+  *out = c;
+  return PTYCHO_OK;
+}
+
+int ptycho_destroy(ptycho_ctx* c) {
+  if (!c) return PTYCHO_OK;
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  cudaFree(c->arena);
+  cudaFree(c->gO);
+  cudaFree(c->gP);
+  cudaFree(c->status);
+  cudaFree(c->Hc);
+  delete c;
+  return PTYCHO_OK;
+}
+
+size_t ptycho_scratch_bytes(const ptycho_geom* geom, int32_t B, int32_t waves) {
+  if (validate_geom(geom) || B < 0) return 0;
+  const EngineOps* ops = ptycho::engine_for(geom->h);
+  int slots = 148 / ops->G;
+  int dev;
+  if (cudaGetDevice(&dev) == cudaSuccess) slots = ops->resident_clusters(true, false);
+  else cudaGetLastError();
+  return make_layout(*geom, B, waves != PTYCHO_WAVES_RECOMPUTE, slots).total;
+}
+
+int ptycho_forward(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
+                   float* I_out, ptycho_stream stream) {
+  int rc = check_call(c, B);
+  if (rc) return rc;
+  if (B == 0) return PTYCHO_OK;
+  if (!O || !P || !pos || !I_out) return perr(PTYCHO_EINVAL, "NULL array argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
+  float2* Phat = reinterpret_cast<float2*>(c->arena + L.Phat);
+  {
+    Timed t(c, "probe_spectrum", s);
+    CK(c->ops->probe_spectrum(reinterpret_cast<const float2*>(P), Phat, c->g.K, s));
+  }
+  ProblemDesc d = base_desc(c, L, O, pos, nullptr, B, B);
+  d.waves = nullptr;
+  LaunchArgs la = one_problem(c, L, d);
+  {
+    Timed t(c, "forward", s);
+    CK(c->ops->forward(la, std::min(B * c->g.K, c->res_fwd), false, s));
+  }
+  {
+    Timed t(c, "modesum", s);
+    CK(c->ops->modesum(d.A, I_out, B, c->g.K, s));
+  }
+  return PTYCHO_OK;
+}
+
+int ptycho_adjoint(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
+                   const float* I_exp, double* loss_out, ptycho_c64* gO, ptycho_c64* gP, int32_t accumulate,
+                   ptycho_stream stream) {
+  int rc = check_call(c, B);
+  if (rc) return rc;
+  if (!O || !P || (B > 0 && (!pos || !I_exp)) || !gO || !gP) return perr(PTYCHO_EINVAL, "NULL array argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int nl = 0;
+  rc = run_gradient(c, O, P, pos, nullptr, B, B, I_exp, gO, gP, accumulate, s, &nl);
+  if (rc) return rc;
+  if (loss_out) {
+    const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
+    Timed t(c, "finalize", s);
+    CK(ptycho::launch_finalize(reinterpret_cast<double*>(c->arena + L.partials), nl, 0, loss_out, 0, s));
+  }
+  return PTYCHO_OK;
+}
+
+int ptycho_vjp(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
+               const float* gI, ptycho_c64* gO, ptycho_c64* gP, int32_t accumulate, ptycho_stream stream) {
+  int rc = check_call(c, B);
+  if (rc) return rc;
+  if (!O || !P || (B > 0 && (!pos || !gI)) || !gO || !gP) return perr(PTYCHO_EINVAL, "NULL array argument");
+  int nl = 0;
+  return run_gradient(c, O, P, pos, nullptr, B, B, nullptr, gO, gP, accumulate, static_cast<cudaStream_t>(stream),
+                      &nl, true, gI);
+}
+
+static int step_impl(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* st, const ptycho_opt* opt,
+                     const float* pos_all, const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B,
+                     double* stats_out, cudaStream_t s) {
+  if (!O || !P || !st || !opt || !st->mO || !st->vO || !st->mP || !st->vP)
+    return perr(PTYCHO_EINVAL, "NULL argument");
+  if (B > 0 && (!pos_all || !I_exp_all)) return perr(PTYCHO_EINVAL, "NULL positions or patterns");
+  if (!(opt->beta1 >= 0 && opt->beta1 < 1 && opt->beta2 >= 0 && opt->beta2 < 1 && opt->eps >= 0 &&
+        std::isfinite(opt->lr_O) && std::isfinite(opt->lr_P)))
+    return perr(PTYCHO_EINVAL, "bad Adam parameters");
+  const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
+  int nl = 0;
+  int rc = run_gradient(c, O, P, pos_all, idx, B, n_pos, I_exp_all, reinterpret_cast<ptycho_c64*>(c->gO),
+                        reinterpret_cast<ptycho_c64*>(c->gP), 0, s, &nl);
+  if (rc) return rc;
+  double* partials = reinterpret_cast<double*>(c->arena + L.partials);
+  double* stats = stats_out ? stats_out : reinterpret_cast<double*>(c->arena + L.stats);
+  const long long nO = (long long)c->g.S * c->g.H * c->g.W;
+  const long long nP = (long long)c->g.K * c->NP;
+  {
+    Timed t(c, "reduce", s);
+    CK(ptycho::launch_sumsq(c->gO, nO, partials + nl, ptycho::kNormBlocks, s));
+    CK(ptycho::launch_sumsq(c->gP, nP, partials + nl + ptycho::kNormBlocks, ptycho::kNormBlocks, s));
+    CK(ptycho::launch_finalize(partials, nl, 2 * ptycho::kNormBlocks, stats, 1, s));
+  }
+  const int64_t t = st->t + 1;
+  const float bc1 = (float)(1.0 / (1.0 - std::pow((double)opt->beta1, (double)t)));
+  const float bc2 = (float)(1.0 / (1.0 - std::pow((double)opt->beta2, (double)t)));
+  {
+    Timed tm(c, "adam", s);
+    CK(ptycho::launch_adam(reinterpret_cast<float2*>(O), reinterpret_cast<float2*>(st->mO), st->vO, c->gO, nO,
+                           opt->lr_O, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s));
+    if (opt->update_probe)
+      CK(ptycho::launch_adam(reinterpret_cast<float2*>(P), reinterpret_cast<float2*>(st->mP), st->vP, c->gP, nP,
+                             opt->lr_P, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s));
+  }
+  st->t = t;
+  return PTYCHO_OK;
+}
+
+int ptycho_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* st, const ptycho_opt* opt,
+                const float* pos_all, const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B,
+                double* stats_out, ptycho_stream stream) {
+  int rc = check_call(c, B);
+  if (rc) return rc;
+  if (B > 0 && !idx) return perr(PTYCHO_EINVAL, "idx is NULL");
+  if (n_pos < 0) return perr(PTYCHO_EINVAL, "n_pos < 0");
+  return step_impl(c, O, P, st, opt, pos_all, I_exp_all, n_pos, idx, B, stats_out, static_cast<cudaStream_t>(stream));
+}
+
+int ptycho_step_host(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* st, const ptycho_opt* opt,
+                     const float* pos_host, const float* I_exp_host, int32_t B, double* loss_host,
+                     double* gnorm_host, ptycho_stream stream) {
+  int rc = check_call(c, B);
+  if (rc) return rc;
+  if (B > 0 && (!pos_host || !I_exp_host)) return perr(PTYCHO_EINVAL, "NULL host arrays");
+  for (int j = 0; j < B; ++j) {
+    const double y = std::floor((double)pos_host[2 * j] + 0.5), x = std::floor((double)pos_host[2 * j + 1] + 0.5);
+    if (!(y >= 0 && x >= 0 && y + c->N <= c->g.H && x + c->N <= c->g.W))
+      return perr(PTYCHO_EOUTOFBOUNDS, "scan position " + std::to_string(j) + " leaves the object");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
+  float* dpos = reinterpret_cast<float*>(c->arena + L.stage_pos);
+  float* dI = reinterpret_cast<float*>(c->arena + L.stage_I);
+  double* stats = reinterpret_cast<double*>(c->arena + L.stats);
+  if (B > 0) {
+    Timed t(c, "h2d", s);
+    CK(cudaMemcpyAsync(dpos, pos_host, (size_t)B * 2 * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dI, I_exp_host, (size_t)B * c->NP * 4, cudaMemcpyHostToDevice, s));
+  }
+  rc = step_impl(c, O, P, st, opt, dpos, dI, B, nullptr, B, stats, s);
+  if (rc) return rc;
+  double h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, stats, 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (loss_host) *loss_host = h[0];
+  if (gnorm_host) *gnorm_host = h[1];
+  return PTYCHO_OK;
+}
+
+int ptycho_check(ptycho_ctx* c, ptycho_stream stream) {
+  if (!c) return perr(PTYCHO_EINVAL, "context is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaStreamSynchronize(s));
+  unsigned st = 0;
+  CK(cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(c->status, 0, sizeof(unsigned)));
+  if (st & ptycho::PTYCHO_STATUS_OUT_OF_BOUNDS)
+    return perr(PTYCHO_EOUTOFBOUNDS, "a scan window left the object; its item was skipped");
+  return PTYCHO_OK;
+}
+
+int ptycho_set_timing(ptycho_ctx* c, int32_t enable) {
+  if (!c) return perr(PTYCHO_EINVAL, "context is NULL");
+  c->timing = enable != 0;
+  return PTYCHO_OK;
+}
+
+int ptycho_kernel_times(ptycho_ctx* c, const char** names, double* ms, int32_t* launches, int32_t cap) {
+  if (!c) return perr(PTYCHO_EINVAL, "context is NULL");
+  for (auto& p : c->pending) {
+    float f = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&f, p.a, p.b) == cudaSuccess) {
+      c->ms[p.kid] += f;
+      c->launches[p.kid] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->pool.push_back(p.a);
+    c->pool.push_back(p.b);
+  }
+  c->pending.clear();
+  const int n = (int)c->names.size();
+  if (cap < 0) {  // reset
+    std::fill(c->ms.begin(), c->ms.end(), 0.0);
+    std::fill(c->launches.begin(), c->launches.end(), 0);
+    return n;
+  }
+  for (int i = 0; i < std::min(n, (int)cap); ++i) {
+    if (names) names[i] = c->names[i].c_str();
+    if (ms) ms[i] = c->ms[i];
+    if (launches) launches[i] = c->launches[i];
+  }
+  return n;
+}
+
+int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count, ptycho_stream stream) {
+  const EngineOps* ops = ptycho::engine_for(N);
+  if (!ops) return perr(PTYCHO_EINVAL, "N not in {64, 128, 192, 256}");
+  if (dir == 0 || count < 0 || (count > 0 && (!in || !out))) return perr(PTYCHO_EINVAL, "bad arguments");
+  if (count == 0) return PTYCHO_OK;
+  CK(ops->fft_debug(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), count, dir,
+                    static_cast<cudaStream_t>(stream)));
+  return PTYCHO_OK;
+}
+
+const char* ptycho_version(void) { return "libptycho 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// FP64 reductions and the complex Adam update (arXiv 2505.14372 §3.2).
+#include <algorithm>
+
+#include "elementwise.cuh"
+#include "engine.h"
+
+namespace ptycho {
+
+// Block partial sums of |g|^2 over a complex array (FP64).
+__global__ void __launch_bounds__(kRedThreads) k_sumsq(const float2* __restrict__ g, long long n,
+                                                       double* __restrict__ partials) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float2 v = __ldg(g + e);
+    acc += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// out[0] = sum of partials[0..n0), out[1] = sqrt(sum of partials[n0..n0+n1))
+// (fixed summation order: deterministic).
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restrict__ partials, int n0, int n1,
+                                                          double* __restrict__ out, int sqrt_second) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) a += partials[i];
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) b += partials[n0 + i];
+  const double ta = block_sum(a, sh);
+  const double tb = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    out[0] = ta;
+    if (n1 > 0) out[1] = sqrt_second ? sqrt(tb) : tb;
+  }
+}
+
+// Complex Adam: m <- b1 m + (1-b1) g; v <- b2 v + (1-b2)|g|^2;
+// z <- z - lr (m bc1) / (sqrt(v bc2) + eps), bc = 1/(1 - beta^t).
+__global__ void k_adam(float2* __restrict__ z, float2* __restrict__ m, float* __restrict__ v,
+                       const float2* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                       float bc1, float bc2) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float2 gg = g[e];
+    float2 mm = m[e];
+    mm.x = fmaf(b1, mm.x, (1.0f - b1) * gg.x);
+    mm.y = fmaf(b1, mm.y, (1.0f - b1) * gg.y);
+    const float vv = fmaf(b2, v[e], (1.0f - b2) * cabs2(gg));
+    const float den = sqrtf(vv * bc2) + eps;
+    const float s = lr * bc1 / den;
+    float2 zz = z[e];
+    zz.x -= s * mm.x;
+    zz.y -= s * mm.y;
+    z[e] = zz;
+    m[e] = mm;
+    v[e] = vv;
+  }
+}
+
+
+cudaError_t launch_sumsq(const float2* g, long long n, double* partials, int nblocks, cudaStream_t s) {
+  k_sumsq<<<nblocks, kRedThreads, 0, s>>>(g, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out, int sqrt_second,
+                            cudaStream_t s) {
+  k_finalize<<<1, kRedThreads, 0, s>>>(partials, n0, n1, out, sqrt_second);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long long n, float lr, float b1,
+                        float b2, float eps, float bc1, float bc2, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+  k_adam<<<blocks, 256, 0, s>>>(z, m, v, g, n, lr, b1, b2, eps, bc1, bc2);
+  return cudaGetLastError();
+}
+
+}  // namespace ptycho

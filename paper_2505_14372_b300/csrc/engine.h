@@ -1,0 +1,50 @@
+// Host-side table of launchers for one window size (one tile shape).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "launch.h"
+
+namespace ptycho {
+
+struct EngineOps {
+  int N, G, T, R1, R2;
+  size_t smem;
+  cudaError_t (*probe_spectrum)(const float2* P, float2* Phat, int K, cudaStream_t s);
+  cudaError_t (*forward)(const LaunchArgs& L, int clusters, bool store, cudaStream_t s);
+  cudaError_t (*adjoint)(const LaunchArgs& L, int clusters, bool store, cudaStream_t s);
+  cudaError_t (*probe_grad)(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s);
+  cudaError_t (*fft_debug)(const float2* in, float2* out, int count, int dir, cudaStream_t s);
+  cudaError_t (*modesum)(const float2* A, float* I, int B, int K, cudaStream_t s);
+  cudaError_t (*loss)(const float2* A, const float* Iexp, const int* idx, int npos, int B, int K, int model,
+                      float eps, float c, float* w, double* partials, int nblocks, cudaStream_t s);
+  cudaError_t (*seed)(const float* gI, int B, float* w, cudaStream_t s);
+  // resident clusters of the forward / adjoint kernels on the current device
+  int (*resident_clusters)(bool adjoint, bool store);
+};
+
+const EngineOps* engine_64();
+const EngineOps* engine_128();
+const EngineOps* engine_192();
+const EngineOps* engine_256();
+
+inline const EngineOps* engine_for(int N) {
+  switch (N) {
+    case 64: return engine_64();
+    case 128: return engine_128();
+    case 192: return engine_192();
+    case 256: return engine_256();
+    default: return nullptr;
+  }
+}
+
+// elementwise launchers (elementwise.cu)
+cudaError_t launch_sumsq(const float2* g, long long n, double* partials, int nblocks, cudaStream_t s);
+cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out, int sqrt_second,
+                            cudaStream_t s);
+cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long long n, float lr, float b1,
+                        float b2, float eps, float bc1, float bc2, cudaStream_t s);
+
+constexpr int kLossBlocks = 1184;  // 148 SMs x 8 resident reduction blocks
+constexpr int kNormBlocks = 592;
+
+}  // namespace ptycho

@@ -1,0 +1,115 @@
+// Launchers of one tile shape; included once per window size.
+#pragma once
+#include <algorithm>
+
+#include "elementwise.cuh"
+#include "engine.h"
+#include "kernels.cuh"
+
+namespace ptycho {
+
+template <class TL>
+struct Engine {
+  template <class K>
+  static cudaError_t launch(K kernel, int clusters, cudaStream_t s, auto... args) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * TL::G), 1, 1);
+    cfg.blockDim = dim3(TL::T, 1, 1);
+    cfg.dynamicSmemBytes = TL::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = TL::G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = TL::G > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+  }
+
+  template <class K>
+  static int resident(K kernel) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM) != cudaSuccess)
+      return std::max(1, nsm / TL::G);
+    if constexpr (TL::G > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(nsm / TL::G * TL::G), 1, 1);
+      cfg.blockDim = dim3(TL::T, 1, 1);
+      cfg.dynamicSmemBytes = TL::SMEM;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = TL::G;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return std::max(1, nsm / TL::G);
+      }
+      return n;
+    } else {
+      int per = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, TL::T, TL::SMEM) != cudaSuccess || per <= 0) {
+        cudaGetLastError();
+        return nsm;
+      }
+      return per * nsm;
+    }
+  }
+
+  static cudaError_t probe_spectrum(const float2* P, float2* Phat, int K, cudaStream_t s) {
+    return launch(k_probe_spectrum<TL>, K, s, P, Phat, K);
+  }
+  static cudaError_t forward(const LaunchArgs& L, int clusters, bool store, cudaStream_t s) {
+    if (store) return launch(k_forward<TL, true>, clusters, s, L);
+    return launch(k_forward<TL, false>, clusters, s, L);
+  }
+  static cudaError_t adjoint(const LaunchArgs& L, int clusters, bool store, cudaStream_t s) {
+    if (store) return launch(k_adjoint<TL, true>, clusters, s, L);
+    return launch(k_adjoint<TL, false>, clusters, s, L);
+  }
+  static cudaError_t probe_grad(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s) {
+    return launch(k_probe_grad<TL>, K, s, gPhat, gP, K, acc);
+  }
+  static cudaError_t fft_debug(const float2* in, float2* out, int count, int dir, cudaStream_t s) {
+    const int cl = std::min(count, resident(k_fft_debug<TL>));
+    return launch(k_fft_debug<TL>, std::max(cl, 1), s, in, out, count, dir);
+  }
+  static cudaError_t modesum(const float2* A, float* I, int B, int K, cudaStream_t s) {
+    const long long n = (long long)B * TL::NP;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+    k_modesum<TL><<<blocks, 256, 0, s>>>(A, I, B, K);
+    return cudaGetLastError();
+  }
+  static cudaError_t loss(const float2* A, const float* Iexp, const int* idx, int npos, int B, int K, int model,
+                          float eps, float c, float* w, double* partials, int nblocks, cudaStream_t s) {
+    k_loss<TL><<<nblocks, kRedThreads, 0, s>>>(A, Iexp, idx, npos, B, K, model, eps, c, w, partials);
+    return cudaGetLastError();
+  }
+  static cudaError_t seed(const float* gI, int B, float* w, cudaStream_t s) {
+    const long long n = (long long)B * TL::NP;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+    k_seed<TL><<<blocks, 256, 0, s>>>(gI, B, w);
+    return cudaGetLastError();
+  }
+  static int resident_clusters(bool adj, bool store) {
+    if (adj) return store ? resident(k_adjoint<TL, true>) : resident(k_adjoint<TL, false>);
+    return store ? resident(k_forward<TL, true>) : resident(k_forward<TL, false>);
+  }
+
+  static const EngineOps* ops() {
+    static const EngineOps o = {TL::N,         TL::G,      TL::T,       TL::R1,      TL::R2,
+                                TL::SMEM,      &probe_spectrum, &forward, &adjoint,  &probe_grad,
+                                &fft_debug,    &modesum,   &loss,       &seed,       &resident_clusters};
+    return &o;
+  }
+};
+
+}  // namespace ptycho

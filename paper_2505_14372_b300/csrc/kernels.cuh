@@ -1,0 +1,357 @@
+// Kernels of the batched mixed-state multislice forward model and its
+// adjoint (arXiv 2505.14372 §3, §3.1, §3.2), one template per tile shape.
+//
+// A work item is one (scan position j, probe mode k) pair of one problem
+// descriptor; a cluster of G CTAs owns one item at a time and keeps its
+// wavefield in shared memory across all slices.  Items of several problems
+// with the same window size may share one launch (serving).
+#pragma once
+#include <stdint.h>
+
+#include "launch.h"
+#include "tile.cuh"
+
+namespace ptycho {
+
+__device__ __forceinline__ const ProblemDesc& find_desc(const LaunchArgs& L, int item) {
+  int d = 0;
+#pragma unroll 1
+  while (d + 1 < L.nd && item >= L.d[d + 1].item0) ++d;
+  return L.d[d];
+}
+
+// Patch origin n = floor(r + 1/2) and subpixel part r - n (FP64).
+struct ItemGeo {
+  int j, jj, k, ny, nx;
+  double dy, dx;
+  bool ok;
+};
+
+template <class TL>
+__device__ __forceinline__ ItemGeo item_geo(const ProblemDesc& D, int item) {
+  ItemGeo g;
+  const int local = item - D.item0;
+  g.j = local / D.K;
+  g.k = local - g.j * D.K;
+  g.jj = D.idx ? D.idx[g.j] : g.j;
+  if (g.jj < 0 || g.jj >= D.npos) {
+    g.ok = false;
+    g.ny = g.nx = 0;
+    g.dy = g.dx = 0.0;
+    return g;
+  }
+  const double ry = (double)D.pos[2 * (size_t)g.jj], rx = (double)D.pos[2 * (size_t)g.jj + 1];
+  const double fy = floor(ry + 0.5), fx = floor(rx + 0.5);
+  g.dy = ry - fy;
+  g.dx = rx - fx;
+  g.ok = fy >= 0.0 && fx >= 0.0 && fy + TL::N <= (double)D.H && fx + TL::N <= (double)D.W;
+  g.ny = g.ok ? (int)fy : 0;
+  g.nx = g.ok ? (int)fx : 0;
+  return g;
+}
+
+// Separable Fourier phase ramp exp(-2 pi i f delta / N) per spectral slot;
+// the phase is formed in turns in FP64 and reduced to [-1/2, 1/2] first.
+template <class TL>
+__device__ __forceinline__ void make_ramps(float2* rampY, float2* rampX, double dy, double dx) {
+  for (int p = threadIdx.x; p < TL::N; p += TL::T) {
+    const double f = (double)TL::freq(TL::nat(p));
+    double ty = f * dy / (double)TL::N, tx = f * dx / (double)TL::N;
+    ty -= rint(ty);
+    tx -= rint(tx);
+    float s, c;
+    sincospif(-2.0f * (float)ty, &s, &c);
+    rampY[p] = make_float2(c, s);
+    sincospif(-2.0f * (float)tx, &s, &c);
+    rampX[p] = make_float2(c, s);
+  }
+}
+
+template <class TL>
+struct Smem {
+  float2* wave;
+  float2* twS;
+  float2* twC;
+  float2* rampY;
+  float2* rampX;
+  float2* chirp;  // [2][N]
+  int* fsq;
+  __device__ Smem(float4* raw) {
+    wave = reinterpret_cast<float2*>(raw);
+    twS = wave + TL::WAVE;
+    twC = twS + TL::N;
+    rampY = twC + TL::N;
+    rampX = rampY + TL::N;
+    chirp = rampX + TL::N;
+    fsq = reinterpret_cast<int*>(chirp + 2 * TL::N);
+  }
+};
+
+template <class TL>
+__device__ __forceinline__ void load_chirp(float2* dst, const float2* src) {
+  for (int p = threadIdx.x; p < TL::N; p += TL::T) dst[p] = src[p];
+}
+
+// Propagator product on the spectral side: H(pu,pv) = h[pu] h[pv] B(pu,pv) / NP
+// (CONJ: its conjugate, for the adjoint).
+template <class TL, bool CONJ>
+struct PropOp {
+  const float2* h;
+  const int* fsq;
+  int blT;
+  __device__ void operator()(int pu, int pv, float2& v) const {
+    const bool keep = blT < 0 || fsq[pu] + fsq[pv] <= blT;
+    const float2 hh = cmul(h[pu], h[pv]);
+    const float s = keep ? 1.0f / (float)TL::NP : 0.0f;
+    v = CONJ ? cscale(cmulc(v, hh), s) : cscale(cmul(v, hh), s);
+  }
+};
+
+// One full forward pass of item (j, k) from the shifted probe to the far
+// field.  The entry wave psi_s of every slice is written to `waves` (natural
+// order, NP per slice) when it is non-null.  On return the column layout
+// holds F(phi_{S-1}) after its column s1 stage: the caller applies the last
+// column s2 (far field) with its own pointwise op.
+template <class TL>
+__device__ void forward_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D, const ItemGeo& g,
+                              float2* waves) {
+  constexpr int N = TL::N;
+  const float inv = 1.0f / (float)TL::NP;
+  const float2* Ph = D.Phat + (size_t)g.k * TL::NP;
+  const float2* rY = sm.rampY;
+  const float2* rX = sm.rampX;
+  // psi_0 = F^-1[ramp . F P_k]: column s2' straight from the stored spectrum
+  TL::template col_contig<false, false, true>(
+      sm.wave, sm.twC, rank,
+      [&](int pu, int pv) { return cscale(cmul(cmul(__ldg(Ph + pu * N + pv), rY[pu]), rX[pv]), inv); },
+      NoOp{});
+  __syncthreads();
+  TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+#pragma unroll 1
+  for (int s = 0; s < D.S; ++s) {
+    if (s + 1 < D.S) load_chirp<TL>(sm.chirp + (s & 1) * N, D.Hc + (size_t)s * N);
+    const float2* Os = D.O + (size_t)s * D.H * D.W + (size_t)g.ny * D.W + g.nx;
+    float2* wv = waves ? waves + (size_t)s * TL::NP : nullptr;
+    const int W = D.W;
+    // row s1' (finishing psi_s) -> store psi_s -> transmit -> row s1
+    TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, [&](int r, int c, float2& v) {
+      if (wv) wv[r * N + c] = v;
+      v = cmul(v, __ldg(Os + (size_t)r * W + c));
+    });
+    __syncthreads();
+    TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
+    if (s + 1 < D.S) {
+      TL::template col_contig<true, true, true>(sm.wave, sm.twC, rank, NoLoad{},
+                                                PropOp<TL, false>{sm.chirp + (s & 1) * N, sm.fsq, D.blT});
+      __syncthreads();
+      TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+    }
+  }
+}
+
+// Backward pass of item (j, k) from g_phi_{S-1} (row layout, pending row
+// s1') to the probe spectrum gradient.  psi_s are read from `waves`.
+template <class TL>
+__device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D, const ItemGeo& g,
+                              const float2* waves) {
+  constexpr int N = TL::N;
+#pragma unroll 1
+  for (int s = D.S - 1; s >= 0; --s) {
+    if (s > 0) load_chirp<TL>(sm.chirp + (s & 1) * N, D.Hc + (size_t)(s - 1) * N);
+    const size_t ooff = (size_t)s * D.H * D.W + (size_t)g.ny * D.W + g.nx;
+    const float2* Os = D.O + ooff;
+    float2* gOs = D.gO + ooff;
+    const float2* wv = waves + (size_t)s * TL::NP;
+    const int W = D.W;
+    // row s1' (finishing g_phi_s) -> object gradient, g_psi_s = conj(O) g_phi -> row s1
+    TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, [&](int r, int c, float2& v) {
+      const float2 psi = wv[r * N + c];
+      const size_t o = (size_t)r * W + c;
+      red_add(gOs + o, cconjmul(psi, v));
+      v = cconjmul(__ldg(Os + o), v);
+    });
+    __syncthreads();
+    TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
+    if (s > 0) {
+      TL::template col_contig<true, true, true>(sm.wave, sm.twC, rank, NoLoad{},
+                                                PropOp<TL, true>{sm.chirp + (s & 1) * N, sm.fsq, D.blT});
+      __syncthreads();
+      TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+    } else {
+      // F g_psi_0 -> conj(ramp) -> accumulate the probe spectrum gradient
+      float2* gP = D.gPhat + (size_t)g.k * TL::NP;
+      const float2* rY = sm.rampY;
+      const float2* rX = sm.rampX;
+      TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
+        red_add(gP + pu * N + pv, cmulc(v, cmul(rY[pu], rX[pv])));
+      });
+    }
+  }
+}
+
+template <class TL>
+__device__ __forceinline__ int cluster_id() { return blockIdx.x / TL::G; }
+template <class TL>
+__device__ __forceinline__ int n_clusters() { return gridDim.x / TL::G; }
+template <class TL>
+__device__ __forceinline__ int my_rank() {
+  if constexpr (TL::G > 1) return (int)cluster_rank(); else return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Forward: far field A = F(phi_{S-1}) (unnormalised, spectral slot order) of
+// every item; optionally every entry wave psi_s (STORE).
+template <class TL, bool STORE>
+__global__ void __launch_bounds__(TL::T, TL::MINB) k_forward(const __grid_constant__ LaunchArgs L) {
+  extern __shared__ float4 smem_raw[];
+  Smem<TL> sm(smem_raw);
+  const int rank = my_rank<TL>();
+  TL::init_tables(sm.twS, sm.twC, sm.fsq);
+  constexpr int N = TL::N;
+#pragma unroll 1
+  for (int item = cluster_id<TL>(); item < L.total; item += n_clusters<TL>()) {
+    const ProblemDesc& D = find_desc(L, item);
+    const ItemGeo g = item_geo<TL>(D, item);
+    if (!g.ok) {
+      if (threadIdx.x == 0 && rank == 0) atomicOr(L.status, PTYCHO_STATUS_OUT_OF_BOUNDS);
+      continue;
+    }
+    __syncthreads();
+    make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
+    __syncthreads();
+    float2* waves = STORE ? D.waves + ((size_t)g.j * D.K + g.k) * D.S * TL::NP : nullptr;
+    forward_chain<TL>(sm, rank, D, g, waves);
+    float2* Aout = D.A + ((size_t)g.j * D.K + g.k) * TL::NP;
+    TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{},
+                                               [&](int pu, int pv, float2& v) { Aout[pu * N + pv] = v; });
+  }
+}
+
+// Adjoint.  STORE: psi_s come from the forward's store; the seed is
+// w . A from global memory.  Otherwise the forward is recomputed here with
+// psi_s written to this cluster's slot, and the far field is turned into
+// the seed without leaving shared memory.
+template <class TL, bool STORE>
+__global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_constant__ LaunchArgs L) {
+  extern __shared__ float4 smem_raw[];
+  Smem<TL> sm(smem_raw);
+  const int rank = my_rank<TL>();
+  TL::init_tables(sm.twS, sm.twC, sm.fsq);
+  constexpr int N = TL::N;
+#pragma unroll 1
+  for (int item = cluster_id<TL>(); item < L.total; item += n_clusters<TL>()) {
+    const ProblemDesc& D = find_desc(L, item);
+    const ItemGeo g = item_geo<TL>(D, item);
+    if (!g.ok) {
+      if (threadIdx.x == 0 && rank == 0) atomicOr(L.status, PTYCHO_STATUS_OUT_OF_BOUNDS);
+      continue;
+    }
+    __syncthreads();
+    make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
+    __syncthreads();
+    const float* wj = D.w + (size_t)g.j * TL::NP;
+    const float2* waves;
+    if constexpr (STORE) {
+      waves = D.waves + ((size_t)g.j * D.K + g.k) * D.S * TL::NP;
+      const float2* Aj = D.A + ((size_t)g.j * D.K + g.k) * TL::NP;
+      TL::template col_contig<false, false, true>(
+          sm.wave, sm.twC, rank, [&](int pu, int pv) { return cscale(Aj[pu * N + pv], wj[pu * N + pv]); },
+          NoOp{});
+      __syncthreads();
+    } else {
+      float2* slot = L.slots + (size_t)cluster_id<TL>() * L.slot_stride;
+      waves = slot;
+      forward_chain<TL>(sm, rank, D, g, slot);
+      TL::template col_contig<true, true, true>(sm.wave, sm.twC, rank, NoLoad{},
+                                                [&](int pu, int pv, float2& v) { v = cscale(v, wj[pu * N + pv]); });
+      __syncthreads();
+    }
+    TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+    adjoint_chain<TL>(sm, rank, D, g, waves);
+  }
+}
+
+// Probe spectra P^_k = F P_k in spectral slot order (one item per mode).
+template <class TL>
+__global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_spectrum(const float2* __restrict__ P, float2* __restrict__ Phat, int K) {
+  extern __shared__ float4 smem_raw[];
+  Smem<TL> sm(smem_raw);
+  const int rank = my_rank<TL>();
+  TL::init_tables(sm.twS, sm.twC, sm.fsq);
+  __syncthreads();
+  constexpr int N = TL::N;
+#pragma unroll 1
+  for (int k = cluster_id<TL>(); k < K; k += n_clusters<TL>()) {
+    const float2* Pk = P + (size_t)k * TL::NP;
+    float2* out = Phat + (size_t)k * TL::NP;
+    __syncthreads();
+    TL::template row_strided<false, true>(sm.wave, sm.twS, rank,
+                                          [&](int r, int c) { return Pk[r * N + c]; }, NoOp{});
+    __syncthreads();
+    TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
+    TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{},
+                                               [&](int pu, int pv, float2& v) { out[pu * N + pv] = v; });
+  }
+}
+
+// Probe gradient g_P_k = F^-1 g_P^_k (natural order); ACC adds to gP.
+template <class TL>
+__global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_grad(const float2* __restrict__ gPhat, float2* __restrict__ gP, int K, int acc) {
+  extern __shared__ float4 smem_raw[];
+  Smem<TL> sm(smem_raw);
+  const int rank = my_rank<TL>();
+  TL::init_tables(sm.twS, sm.twC, sm.fsq);
+  __syncthreads();
+  constexpr int N = TL::N;
+  const float inv = 1.0f / (float)TL::NP;
+#pragma unroll 1
+  for (int k = cluster_id<TL>(); k < K; k += n_clusters<TL>()) {
+    const float2* src = gPhat + (size_t)k * TL::NP;
+    float2* out = gP + (size_t)k * TL::NP;
+    __syncthreads();
+    TL::template col_contig<false, false, true>(sm.wave, sm.twC, rank,
+                                                [&](int pu, int pv) { return src[pu * N + pv]; }, NoOp{});
+    __syncthreads();
+    TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+    TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{}, [&](int r, int c, float2& v) {
+      const float2 x = cscale(v, inv);
+      out[r * N + c] = acc ? cadd(out[r * N + c], x) : x;
+    });
+  }
+}
+
+// Stand-alone 2-D DFT of natural-order arrays through the tile (tests).
+// dir < 0: unnormalised forward; dir > 0: unnormalised inverse.
+template <class TL>
+__global__ void __launch_bounds__(TL::T, TL::MINB) k_fft_debug(const float2* __restrict__ in, float2* __restrict__ out, int count, int dir) {
+  extern __shared__ float4 smem_raw[];
+  Smem<TL> sm(smem_raw);
+  const int rank = my_rank<TL>();
+  TL::init_tables(sm.twS, sm.twC, sm.fsq);
+  __syncthreads();
+  constexpr int N = TL::N;
+#pragma unroll 1
+  for (int b = cluster_id<TL>(); b < count; b += n_clusters<TL>()) {
+    const float2* x = in + (size_t)b * TL::NP;
+    float2* y = out + (size_t)b * TL::NP;
+    __syncthreads();
+    if (dir < 0) {
+      TL::template row_strided<false, true>(sm.wave, sm.twS, rank, [&](int r, int c) { return x[r * N + c]; },
+                                            NoOp{});
+      __syncthreads();
+      TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
+      TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
+        y[TL::nat(pu) * N + TL::nat(pv)] = v;
+      });
+    } else {
+      TL::template col_contig<false, false, true>(
+          sm.wave, sm.twC, rank, [&](int pu, int pv) { return x[TL::nat(pu) * N + TL::nat(pv)]; }, NoOp{});
+      __syncthreads();
+      TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+      TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{},
+                                            [&](int r, int c, float2& v) { y[r * N + c] = v; });
+    }
+  }
+}
+
+}  // namespace ptycho

@@ -1,0 +1,38 @@
+// Launch descriptors shared by the host runtime and the kernels.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+namespace ptycho {
+
+constexpr int kMaxDesc = 16;           // problems per batched launch
+constexpr unsigned PTYCHO_STATUS_OUT_OF_BOUNDS = 1u;
+
+// One problem (dataset) inside a launch.  All pointers are device pointers.
+struct ProblemDesc {
+  const float2* O;      // [S][H][W] object slices
+  const float2* Phat;   // [K][NP] probe spectra, spectral slot order
+  const float* pos;     // [*][2] scan positions (y, x), window top-left
+  const int* idx;       // [B] minibatch -> position index (null: identity)
+  const float2* Hc;     // [S-1][N] separable Fresnel chirp per gap, slot order
+  float2* A;            // [B][K][NP] far field F(phi), slot order
+  const float* w;       // [B][NP] 2 l'(I) / NP, slot order (adjoint)
+  float2* waves;        // STORE: [B][K][S][NP] entry waves (natural order)
+  float2* gO;           // [S][H][W] object gradient (accumulated)
+  float2* gPhat;        // [K][NP] probe spectrum gradient (accumulated)
+  int S, K, H, W, B;
+  int npos;             // rows of pos (and of the pattern array) idx may select
+  int blT;              // band limit keeps f_u^2 + f_v^2 <= blT; < 0: off
+  int item0;            // first global item of this problem
+};
+
+struct LaunchArgs {
+  ProblemDesc d[kMaxDesc];
+  int nd;
+  int total;                // items over all problems
+  unsigned* status;         // device status word (PTYCHO_STATUS_*)
+  float2* slots;            // recompute scratch, one slot per cluster
+  long long slot_stride;    // float2 per slot
+};
+
+}  // namespace ptycho

@@ -1,0 +1,306 @@
+// Shared-memory resident 2-D FFT tile for one N x N complex64 wavefield.
+//
+// One wavefield lives in the shared memory of a cluster of G CTAs (G = 1 for
+// N <= 128; G = 2 for 192; G = 4 for 256, because 192^2 and 256^2 complex64
+// waves exceed one SM's 227 KB).  Every 1-D transform is split N = R1 * R2:
+//   forward:  strided stage   (R1-point DFT over elements n2 + R2*n1, then
+//                              twiddle W_N^(n2 k1)),
+//             contiguous stage (R2-point DFT over the R2 consecutive slots of
+//                              group k1); the spectrum is left in digit-
+//                              permuted order: slot k2 + R2*k1 holds bin
+//                              k1 + R1*k2.
+//   inverse:  contiguous stage (inverse R2-point DFT, twiddle W_N^-(n2 k1)),
+//             strided stage   (inverse R1-point DFT), natural order out.
+// All stages are in place, so FFT -> pointwise product -> inverse FFT (one
+// multislice propagation) never reorders data, and the pointwise ops are
+// fused into the stages that touch the data anyway.
+//
+// Layouts (per CTA of rank c): the smem holds G blocks of ROWS x ROWS
+// (ROWS = N/G).  Row layout: block b = (my rows) x (columns of CTA b).
+// Column layout: block b = (rows of CTA b) x (my columns).  Switching layout
+// is a block transpose across the cluster: element (CTA c, block b, offset o)
+// moves to (CTA b, block c, offset o); it is fused into the last stage of a
+// row pass (row -> column) and of an inverse column pass (column -> row),
+// written with st.shared::cluster into the partner's smem between two
+// cluster barriers.  Rows of a block are padded so that every stage's shared
+// memory accesses are free of bank conflicts.
+#pragma once
+#include <stdint.h>
+
+#include "radix.cuh"
+
+namespace ptycho {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// fire-and-forget vector reduction into global memory (sm_90+)
+__device__ __forceinline__ void red_add(float2* p, float2 v) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+
+struct NoLoad {
+  __device__ float2 operator()(int, int) const { return make_float2(0.f, 0.f); }
+};
+struct NoOp {
+  __device__ void operator()(int, int, float2&) const {}
+};
+
+template <int N_, int G_, int R1_, int R2_, int T_, int MINB_ = 1>
+struct Tile {
+  static constexpr int N = N_, G = G_, R1 = R1_, R2 = R2_, T = T_, MINB = MINB_;
+  static constexpr int NP = N * N;
+  static constexpr int ROWS = N / G;
+  static constexpr int NB = ROWS / R2;               // R2-groups per block row
+  static constexpr int LDB0 = ROWS + NB;             // one pad slot per group
+  static constexpr int LDB = LDB0 + ((8 - LDB0 % 16) % 16 + 16) % 16;  // == 8 mod 16
+  static constexpr int BLK0 = ROWS * LDB;
+  static constexpr int BLK = G == 1 ? BLK0 : BLK0 + ((16 / G - BLK0 % 16) % 16 + 16) % 16;
+  static constexpr int WAVE = G * BLK;               // float2 slots per CTA
+  static constexpr int SPT = ROWS * R2 / T;          // strided tasks per thread
+  static constexpr int CPT = ROWS * R1 / T;          // contiguous tasks per thread
+  // smem: wave, twS[N], twC[N], rampY[N], rampX[N], chirp[2][N], fsq[N] (int)
+  static constexpr size_t SMEM = sizeof(float2) * (WAVE + 6 * N) + sizeof(int) * N;
+  static_assert(N == R1 * R2, "N = R1 R2");
+  static_assert(N % G == 0 && ROWS % R2 == 0, "block split");
+  static_assert((ROWS * R2) % T == 0 && (ROWS * R1) % T == 0, "whole tasks per thread");
+
+  // natural DFT bin held by spectral slot p, and slot of natural bin n
+  __host__ __device__ static constexpr int nat(int p) { return p / R2 + R1 * (p % R2); }
+  __host__ __device__ static constexpr int perm(int n) { return n / R1 + R2 * (n % R1); }
+  // signed DFT frequency (fftfreq order) of natural bin n
+  __host__ __device__ static constexpr int freq(int n) { return n < (N + 1) / 2 ? n : n - N; }
+
+  __device__ static constexpr int phys(int cc) { return cc + cc / R2; }
+  __device__ static constexpr int rs_off(int n1) { return (n1 / NB) * BLK + (R2 + 1) * (n1 % NB); }
+  __device__ static constexpr int cs_off(int n1) { return (n1 / NB) * BLK + R2 * (n1 % NB) * LDB; }
+
+  __device__ static void sync_cta() { __syncthreads(); }
+  __device__ static void sync_cluster() {
+    if constexpr (G > 1) cluster_barrier(); else __syncthreads();
+  }
+
+  // Twiddles W_N^(n2 k1) = exp(-2 pi i n2 k1 / N): twS[k1*R2 + n2] (strided
+  // stage, lanes over n2) and twC[n2*R1 + k1] (contiguous stage, lanes over
+  // k1); fsq[p] = freq(nat(p))^2 for the band limit.
+  __device__ static void init_tables(float2* twS, float2* twC, int* fsq) {
+    for (int i = threadIdx.x; i < N; i += T) {
+      const int k1 = i / R2, n2 = i % R2;
+      double s, c;
+      sincospi(-2.0 * (double)(n2 * k1) / (double)N, &s, &c);
+      twS[i] = make_float2((float)c, (float)s);
+      const int n2b = i / R1, k1b = i % R1;
+      sincospi(-2.0 * (double)(n2b * k1b) / (double)N, &s, &c);
+      twC[i] = make_float2((float)c, (float)s);
+      const int f = freq(nat(i));
+      fsq[i] = f * f;
+    }
+  }
+
+  // Row strided stage over the CTA's ROWS rows.  FROM_SMEM: the values are
+  // the inverse s1' of the slots (natural columns out); otherwise load(grow,
+  // col).  op(grow, col, v) sees natural real-space samples.  TO_SMEM: the
+  // forward s1 (R1-point DFT + twiddle) is written back in place.
+  template <bool FROM_SMEM, bool TO_SMEM, class Load, class Op>
+  __device__ static void row_strided(float2* wave, const float2* twS, int rank, const Load& load,
+                                     const Op& op) {
+#pragma unroll 1
+    for (int t = 0; t < SPT; ++t) {
+      const int id = threadIdx.x + t * T;
+      const int r = id / R2, n2 = id % R2;
+      const int base = r * LDB + n2;
+      const int grow = rank * ROWS + r;
+      float2 x[R1];
+      if constexpr (FROM_SMEM) {
+#pragma unroll
+        for (int i = 0; i < R1; ++i) x[i] = wave[base + rs_off(i)];
+        Dft<R1, +1>::run(x);
+      } else {
+#pragma unroll
+        for (int i = 0; i < R1; ++i) x[i] = load(grow, n2 + R2 * i);
+      }
+#pragma unroll
+      for (int i = 0; i < R1; ++i) op(grow, n2 + R2 * i, x[i]);
+      if constexpr (TO_SMEM) {
+        Dft<R1, -1>::run(x);
+#pragma unroll
+        for (int k = 1; k < R1; ++k) x[k] = cmul(x[k], twS[k * R2 + n2]);
+#pragma unroll
+        for (int i = 0; i < R1; ++i) wave[base + rs_off(i)] = x[i];
+      }
+    }
+  }
+
+  // Row contiguous stage.  DIR < 0: forward s2, result to the column layout
+  // (cluster block transpose when G > 1).  DIR > 0: inverse s2' + twiddle, in
+  // place.  Ends with the barrier its result needs.
+  template <int DIR>
+  __device__ static void row_contig(float2* wave, const float2* twC, int rank) {
+    if constexpr (DIR < 0 && G > 1) {
+      float2 x[CPT][R2];
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        const int id = threadIdx.x + t * T;
+        const int r = id / R1, k1 = id % R1;
+        const int o = (k1 / NB) * BLK + r * LDB + (R2 + 1) * (k1 % NB);
+#pragma unroll
+        for (int i = 0; i < R2; ++i) x[t][i] = wave[o + i];
+        Dft<R2, -1>::run(x[t]);
+      }
+      cluster_barrier();
+      const uint32_t w0 = smem_u32(wave);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        const int id = threadIdx.x + t * T;
+        const int r = id / R1, k1 = id % R1;
+        const int o = rank * BLK + r * LDB + (R2 + 1) * (k1 % NB);
+        const uint32_t dst = cluster_map(w0 + 8u * (uint32_t)o, (uint32_t)(k1 / NB));
+#pragma unroll
+        for (int i = 0; i < R2; ++i) st_cluster(dst + 8u * i, x[t][i]);
+      }
+      cluster_barrier();
+    } else {
+#pragma unroll 1
+      for (int t = 0; t < CPT; ++t) {
+        const int id = threadIdx.x + t * T;
+        const int r = id / R1, k1 = id % R1;
+        const int o = (k1 / NB) * BLK + r * LDB + (R2 + 1) * (k1 % NB);
+        float2 x[R2];
+#pragma unroll
+        for (int i = 0; i < R2; ++i) x[i] = wave[o + i];
+        Dft<R2, DIR>::run(x);
+        if constexpr (DIR > 0) {
+#pragma unroll
+          for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
+        }
+#pragma unroll
+        for (int i = 0; i < R2; ++i) wave[o + i] = x[i];
+      }
+      __syncthreads();
+    }
+  }
+
+  // Column strided stage.  DIR < 0: forward s1 (DFT + twiddle) in place.
+  // DIR > 0: inverse s1', natural rows, result to the row layout (cluster
+  // block transpose when G > 1).  Ends with the barrier its result needs.
+  template <int DIR>
+  __device__ static void col_strided(float2* wave, const float2* twS, int rank) {
+    if constexpr (DIR > 0 && G > 1) {
+      float2 x[SPT][R1];
+#pragma unroll
+      for (int t = 0; t < SPT; ++t) {
+        const int id = threadIdx.x + t * T;
+        const int n2 = id / ROWS, cc = id % ROWS;
+        const int base = n2 * LDB + phys(cc);
+#pragma unroll
+        for (int i = 0; i < R1; ++i) x[t][i] = wave[base + cs_off(i)];
+        Dft<R1, +1>::run(x[t]);
+      }
+      cluster_barrier();
+      const uint32_t w0 = smem_u32(wave);
+#pragma unroll
+      for (int t = 0; t < SPT; ++t) {
+        const int id = threadIdx.x + t * T;
+        const int n2 = id / ROWS, cc = id % ROWS;
+        const int base = rank * BLK + n2 * LDB + phys(cc);
+#pragma unroll
+        for (int i = 0; i < R1; ++i) {
+          const uint32_t dst = cluster_map(w0 + 8u * (uint32_t)(base + R2 * (i % NB) * LDB),
+                                           (uint32_t)(i / NB));
+          st_cluster(dst, x[t][i]);
+        }
+      }
+      cluster_barrier();
+    } else {
+#pragma unroll 1
+      for (int t = 0; t < SPT; ++t) {
+        const int id = threadIdx.x + t * T;
+        const int n2 = id / ROWS, cc = id % ROWS;
+        const int base = n2 * LDB + phys(cc);
+        float2 x[R1];
+#pragma unroll
+        for (int i = 0; i < R1; ++i) x[i] = wave[base + cs_off(i)];
+        if constexpr (DIR < 0) {
+          Dft<R1, -1>::run(x);
+#pragma unroll
+          for (int k = 1; k < R1; ++k) x[k] = cmul(x[k], twS[k * R2 + n2]);
+        } else {
+          Dft<R1, +1>::run(x);
+        }
+#pragma unroll
+        for (int i = 0; i < R1; ++i) wave[base + cs_off(i)] = x[i];
+      }
+      __syncthreads();
+    }
+  }
+
+  // Column contiguous stage on the spectral side.  Values come from the slots
+  // (FROM_SMEM) or load(pu, pv); FWD applies the forward s2 so that register
+  // i holds spectral slot pu = R2 k1 + i; op(pu, pv, v) is the pointwise
+  // product; INV applies inverse s2' + twiddle and writes back in place.
+  template <bool FROM_SMEM, bool FWD, bool INV, class Load, class Op>
+  __device__ static void col_contig(float2* wave, const float2* twC, int rank, const Load& load,
+                                    const Op& op) {
+#pragma unroll 1
+    for (int t = 0; t < CPT; ++t) {
+      const int id = threadIdx.x + t * T;
+      const int k1 = id / ROWS, cc = id % ROWS;
+      const int base = (k1 / NB) * BLK + R2 * (k1 % NB) * LDB + phys(cc);
+      const int pv = rank * ROWS + cc;
+      const int pu0 = R2 * k1;
+      float2 x[R2];
+      if constexpr (FROM_SMEM) {
+#pragma unroll
+        for (int i = 0; i < R2; ++i) x[i] = wave[base + i * LDB];
+      } else {
+#pragma unroll
+        for (int i = 0; i < R2; ++i) x[i] = load(pu0 + i, pv);
+      }
+      if constexpr (FWD) Dft<R2, -1>::run(x);
+#pragma unroll
+      for (int i = 0; i < R2; ++i) op(pu0 + i, pv, x[i]);
+      if constexpr (INV) {
+        Dft<R2, +1>::run(x);
+#pragma unroll
+        for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
+#pragma unroll
+        for (int i = 0; i < R2; ++i) wave[base + i * LDB] = x[i];
+      }
+    }
+  }
+
+  // ---- composite passes -------------------------------------------------
+  // Inverse 2-D transform from a spectrum already in the column layout,
+  // after its contiguous stage: column s1' (to row layout), row s2'.  The
+  // row s1' is left to the caller (fused with the next pointwise op).
+  __device__ static void inverse_tail(float2* wave, const float2* twS, const float2* twC, int rank) {
+    col_strided<+1>(wave, twS, rank);
+    row_contig<+1>(wave, twC, rank);
+  }
+  // Forward 2-D transform after the row s1 stage: row s2 (to column
+  // layout), column s1.  The column s2 is left to the caller.
+  __device__ static void forward_mid(float2* wave, const float2* twS, const float2* twC, int rank) {
+    row_contig<-1>(wave, twC, rank);
+    col_strided<-1>(wave, twS, rank);
+  }
+};
+
+}  // namespace ptycho

@@ -343,3 +343,19 @@ def test_gradient_fd_on_four_position_multislice_subproblem():
             an = np.real(np.vdot(gP, d))
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - an) < 1e-6 * abs(an), (which, fd, an)
+
+
+def test_vjp_is_gradient_of_linearised_loss():
+    # for L = sum c * I the VJP with gI = c equals the FD derivative of L
+    g = tiny(S=2, K=2)
+    O = phase_obj(2, 12, 12)
+    P = crand(2, 8, 8)
+    cI = RNG.standard_normal((4, 8, 8))
+    gO, gP = orc.vjp(O, P, POS4, cI, g)
+    d = crand(2, 12, 12)
+    h = 1e-6
+    fd = (np.sum(cI * orc.forward(O + h * d, P, POS4, g)) - np.sum(cI * orc.forward(O - h * d, P, POS4, g))) / (2 * h)
+    assert abs(fd - np.real(np.vdot(gO, d))) < 1e-6 * max(1.0, abs(fd))
+    d = crand(2, 8, 8)
+    fd = (np.sum(cI * orc.forward(O, P + h * d, POS4, g)) - np.sum(cI * orc.forward(O, P - h * d, POS4, g))) / (2 * h)
+    assert abs(fd - np.real(np.vdot(gP, d))) < 1e-6 * max(1.0, abs(fd))
