@@ -87,6 +87,28 @@ struct Smem {
   }
 };
 
+// Global operands of the real-space stage, issued before its shared-memory
+// work so that their latency overlaps the inverse DFT.
+struct PreO {
+  const float2* O;
+  int W;
+  using type = float2;
+  __device__ float2 operator()(int r, int c) const { return __ldg(O + (size_t)r * W + c); }
+};
+struct PsiO {
+  float2 psi, o;
+};
+struct PrePsiO {
+  const float2* psi;  // entry wave of the slice, natural order, row stride N
+  int N;
+  const float2* O;
+  int W;
+  using type = PsiO;
+  __device__ PsiO operator()(int r, int c) const {
+    return {__ldcs(psi + r * N + c), __ldg(O + (size_t)r * W + c)};
+  }
+};
+
 template <class TL>
 __device__ __forceinline__ void load_chirp(float2* dst, const float2* src) {
   for (int p = threadIdx.x; p < TL::N; p += TL::T) dst[p] = src[p];
@@ -134,10 +156,12 @@ __device__ void forward_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
     float2* wv = waves ? waves + (size_t)s * TL::NP : nullptr;
     const int W = D.W;
     // row s1' (finishing psi_s) -> store psi_s -> transmit -> row s1
-    TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, [&](int r, int c, float2& v) {
-      if (wv) wv[r * N + c] = v;
-      v = cmul(v, __ldg(Os + (size_t)r * W + c));
-    });
+    TL::template row_strided<true, true>(
+        sm.wave, sm.twS, rank, NoLoad{}, PreO{Os, W},
+        [&](int r, int c, float2& v, const float2& o) {
+          if (wv) wv[r * N + c] = v;
+          v = cmul(v, o);
+        });
     __syncthreads();
     TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
     if (s + 1 < D.S) {
@@ -164,12 +188,12 @@ __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
     const float2* wv = waves + (size_t)s * TL::NP;
     const int W = D.W;
     // row s1' (finishing g_phi_s) -> object gradient, g_psi_s = conj(O) g_phi -> row s1
-    TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, [&](int r, int c, float2& v) {
-      const float2 psi = wv[r * N + c];
-      const size_t o = (size_t)r * W + c;
-      red_add(gOs + o, cconjmul(psi, v));
-      v = cconjmul(__ldg(Os + o), v);
-    });
+    TL::template row_strided<true, true>(
+        sm.wave, sm.twS, rank, NoLoad{}, PrePsiO{wv, N, Os, W},
+        [&](int r, int c, float2& v, const PsiO& p) {
+          red_add(gOs + (size_t)r * W + c, cconjmul(p.psi, v));
+          v = cconjmul(p.o, v);
+        });
     __syncthreads();
     TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
     if (s > 0) {
@@ -286,7 +310,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_spectrum(const float2
     float2* out = Phat + (size_t)k * TL::NP;
     __syncthreads();
     TL::template row_strided<false, true>(sm.wave, sm.twS, rank,
-                                          [&](int r, int c) { return Pk[r * N + c]; }, NoOp{});
+                                          [&](int r, int c) { return Pk[r * N + c]; }, NoPre{}, NoOp4{});
     __syncthreads();
     TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
     TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{},
@@ -313,10 +337,11 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_grad(const float2* __
                                                 [&](int pu, int pv) { return src[pu * N + pv]; }, NoOp{});
     __syncthreads();
     TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
-    TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{}, [&](int r, int c, float2& v) {
-      const float2 x = cscale(v, inv);
-      out[r * N + c] = acc ? cadd(out[r * N + c], x) : x;
-    });
+    TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{}, NoPre{},
+                                          [&](int r, int c, float2& v, const NoPre::type&) {
+                                            const float2 x = cscale(v, inv);
+                                            out[r * N + c] = acc ? cadd(out[r * N + c], x) : x;
+                                          });
   }
 }
 
@@ -337,7 +362,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_fft_debug(const float2* __r
     __syncthreads();
     if (dir < 0) {
       TL::template row_strided<false, true>(sm.wave, sm.twS, rank, [&](int r, int c) { return x[r * N + c]; },
-                                            NoOp{});
+                                            NoPre{}, NoOp4{});
       __syncthreads();
       TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
       TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
@@ -348,8 +373,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_fft_debug(const float2* __r
           sm.wave, sm.twC, rank, [&](int pu, int pv) { return x[TL::nat(pu) * N + TL::nat(pv)]; }, NoOp{});
       __syncthreads();
       TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
-      TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{},
-                                            [&](int r, int c, float2& v) { y[r * N + c] = v; });
+      TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{}, NoPre{},
+                                            [&](int r, int c, float2& v, const NoPre::type&) { y[r * N + c] = v; });
     }
   }
 }

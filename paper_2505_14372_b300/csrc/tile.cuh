@@ -2,7 +2,8 @@
 //
 // One wavefield lives in the shared memory of a cluster of G CTAs (G = 1 for
 // N <= 128; G = 2 for 192; G = 4 for 256, because 192^2 and 256^2 complex64
-// waves exceed one SM's 227 KB).  Every 1-D transform is split N = R1 * R2:
+// waves exceed one SM's 227 KB).  Every 1-D transform is split N = R1 * R2
+// (R2 = 16):
 //   forward:  strided stage   (R1-point DFT over elements n2 + R2*n1, then
 //                              twiddle W_N^(n2 k1)),
 //             contiguous stage (R2-point DFT over the R2 consecutive slots of
@@ -18,12 +19,18 @@
 // Layouts (per CTA of rank c): the smem holds G blocks of ROWS x ROWS
 // (ROWS = N/G).  Row layout: block b = (my rows) x (columns of CTA b).
 // Column layout: block b = (rows of CTA b) x (my columns).  Switching layout
-// is a block transpose across the cluster: element (CTA c, block b, offset o)
-// moves to (CTA b, block c, offset o); it is fused into the last stage of a
-// row pass (row -> column) and of an inverse column pass (column -> row),
-// written with st.shared::cluster into the partner's smem between two
-// cluster barriers.  Rows of a block are padded so that every stage's shared
-// memory accesses are free of bank conflicts.
+// is a block transpose across the cluster: element (CTA c, block b, row r,
+// column cc) moves to (CTA b, block c, r, cc); it is fused into the last
+// stage of a row pass (row -> column) and of an inverse column pass (column
+// -> row), written with st.shared::cluster into the partner's smem between
+// two cluster barriers.
+//
+// Bank conflicts: slot (b, r, cc) sits at b*ROWS^2 + r*ROWS + (cc ^ f) with
+// f = (R1 r + NB b + cc / R2) mod 16, NB = ROWS / R2.  Lanes of a half-warp
+// then hit 16 distinct bank pairs in all four stage patterns: the strided
+// and column stages walk 16 consecutive cc of one row (f constant, the XOR
+// permutes them), and the row-contiguous stage has lanes (r, k1) with
+// f = (R1 r + k1) mod 16 = lane id mod 16.
 #pragma once
 #include <stdint.h>
 
@@ -42,10 +49,17 @@ __device__ __forceinline__ uint32_t cluster_map(uint32_t addr, uint32_t rank) {
 __device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
   asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile(
-      "barrier.cluster.arrive.release.aligned;\n\t"
-      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+// Arrive without ordering memory: used where the partner only needs to know
+// that this CTA has consumed (loaded into registers) the slots it will
+// overwrite.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -63,25 +77,32 @@ struct NoLoad {
 struct NoOp {
   __device__ void operator()(int, int, float2&) const {}
 };
+struct NoPre {
+  struct type {};
+  __device__ type operator()(int, int) const { return {}; }
+};
+struct NoOp4 {
+  template <class P>
+  __device__ void operator()(int, int, float2&, const P&) const {}
+};
 
-template <int N_, int G_, int R1_, int R2_, int T_, int MINB_ = 1>
+template <int N_, int G_, int R2_, int T_, int MINB_ = 1>
 struct Tile {
-  static constexpr int N = N_, G = G_, R1 = R1_, R2 = R2_, T = T_, MINB = MINB_;
+  static constexpr int N = N_, G = G_, R2 = R2_, R1 = N_ / R2_, T = T_, MINB = MINB_;
   static constexpr int NP = N * N;
   static constexpr int ROWS = N / G;
   static constexpr int NB = ROWS / R2;               // R2-groups per block row
-  static constexpr int LDB0 = ROWS + NB;             // one pad slot per group
-  static constexpr int LDB = LDB0 + ((8 - LDB0 % 16) % 16 + 16) % 16;  // == 8 mod 16
-  static constexpr int BLK0 = ROWS * LDB;
-  static constexpr int BLK = G == 1 ? BLK0 : BLK0 + ((16 / G - BLK0 % 16) % 16 + 16) % 16;
+  static constexpr int BLK = ROWS * ROWS;
   static constexpr int WAVE = G * BLK;               // float2 slots per CTA
-  static constexpr int SPT = ROWS * R2 / T;          // strided tasks per thread
-  static constexpr int CPT = ROWS * R1 / T;          // contiguous tasks per thread
+  static constexpr int TS = ROWS * R2;               // strided-stage tasks (R1 elements)
+  static constexpr int TC = ROWS * R1;               // contiguous-stage tasks (R2 elements)
+  static constexpr int SPT = (TS + T - 1) / T;       // strided tasks per thread (last may idle)
+  static constexpr int CPT = (TC + T - 1) / T;       // contiguous tasks per thread
   // smem: wave, twS[N], twC[N], rampY[N], rampX[N], chirp[2][N], fsq[N] (int)
   static constexpr size_t SMEM = sizeof(float2) * (WAVE + 6 * N) + sizeof(int) * N;
-  static_assert(N == R1 * R2, "N = R1 R2");
-  static_assert(N % G == 0 && ROWS % R2 == 0, "block split");
-  static_assert((ROWS * R2) % T == 0 && (ROWS * R1) % T == 0, "whole tasks per thread");
+  static_assert(N == R1 * R2 && R2 % 16 == 0, "N = R1 R2 with R2 a multiple of 16");
+  static_assert(N % G == 0 && ROWS % R2 == 0 && ROWS % 16 == 0, "block split");
+  static_assert(T % 32 == 0, "whole warps");
 
   // natural DFT bin held by spectral slot p, and slot of natural bin n
   __host__ __device__ static constexpr int nat(int p) { return p / R2 + R1 * (p % R2); }
@@ -89,13 +110,10 @@ struct Tile {
   // signed DFT frequency (fftfreq order) of natural bin n
   __host__ __device__ static constexpr int freq(int n) { return n < (N + 1) / 2 ? n : n - N; }
 
-  __device__ static constexpr int phys(int cc) { return cc + cc / R2; }
-  __device__ static constexpr int rs_off(int n1) { return (n1 / NB) * BLK + (R2 + 1) * (n1 % NB); }
-  __device__ static constexpr int cs_off(int n1) { return (n1 / NB) * BLK + R2 * (n1 % NB) * LDB; }
-
-  __device__ static void sync_cta() { __syncthreads(); }
-  __device__ static void sync_cluster() {
-    if constexpr (G > 1) cluster_barrier(); else __syncthreads();
+  // swizzled slot of (block b, row r, column cc) within one CTA
+  __device__ static __forceinline__ int slot(int b, int r, int cc) {
+    const int f = (R1 * r + NB * b + cc / R2) & 15;
+    return b * BLK + r * ROWS + (cc ^ f);
   }
 
   // Twiddles W_N^(n2 k1) = exp(-2 pi i n2 k1 / N): twS[k1*R2 + n2] (strided
@@ -115,36 +133,47 @@ struct Tile {
     }
   }
 
-  // Row strided stage over the CTA's ROWS rows.  FROM_SMEM: the values are
-  // the inverse s1' of the slots (natural columns out); otherwise load(grow,
-  // col).  op(grow, col, v) sees natural real-space samples.  TO_SMEM: the
-  // forward s1 (R1-point DFT + twiddle) is written back in place.
-  template <bool FROM_SMEM, bool TO_SMEM, class Load, class Op>
-  __device__ static void row_strided(float2* wave, const float2* twS, int rank, const Load& load,
+  // Row strided stage over the CTA's ROWS rows.  pre(grow, col) is called
+  // first for every element of a task (global operands, issued before the
+  // shared-memory work); FROM_SMEM: the values are the inverse s1' of the
+  // slots (natural columns out), otherwise load(grow, col).  op(grow, col, v,
+  // pre) sees natural real-space samples.  TO_SMEM: the forward s1 (R1-point
+  // DFT + twiddle) is written back in place.  The caller synchronises.
+  template <bool FROM_SMEM, bool TO_SMEM, class Load, class Pre, class Op>
+  __device__ static void row_strided(float2* wave, const float2* twS, int rank, const Load& load, const Pre& pre,
                                      const Op& op) {
 #pragma unroll 1
     for (int t = 0; t < SPT; ++t) {
       const int id = threadIdx.x + t * T;
+      if (TS % T != 0 && id >= TS) break;
       const int r = id / R2, n2 = id % R2;
-      const int base = r * LDB + n2;
       const int grow = rank * ROWS + r;
+      typename Pre::type pv[R1];
+#pragma unroll
+      for (int i = 0; i < R1; ++i) pv[i] = pre(grow, n2 + R2 * i);
       float2 x[R1];
       if constexpr (FROM_SMEM) {
 #pragma unroll
-        for (int i = 0; i < R1; ++i) x[i] = wave[base + rs_off(i)];
+        for (int i = 0; i < R1; ++i) {
+          const int col = n2 + R2 * i;
+          x[i] = wave[slot(col / ROWS, r, col % ROWS)];
+        }
         Dft<R1, +1>::run(x);
       } else {
 #pragma unroll
         for (int i = 0; i < R1; ++i) x[i] = load(grow, n2 + R2 * i);
       }
 #pragma unroll
-      for (int i = 0; i < R1; ++i) op(grow, n2 + R2 * i, x[i]);
+      for (int i = 0; i < R1; ++i) op(grow, n2 + R2 * i, x[i], pv[i]);
       if constexpr (TO_SMEM) {
         Dft<R1, -1>::run(x);
 #pragma unroll
         for (int k = 1; k < R1; ++k) x[k] = cmul(x[k], twS[k * R2 + n2]);
 #pragma unroll
-        for (int i = 0; i < R1; ++i) wave[base + rs_off(i)] = x[i];
+        for (int i = 0; i < R1; ++i) {
+          const int col = n2 + R2 * i;
+          wave[slot(col / ROWS, r, col % ROWS)] = x[i];
+        }
       }
     }
   }
@@ -159,40 +188,53 @@ struct Tile {
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
         const int id = threadIdx.x + t * T;
+        if (TC % T != 0 && id >= TC) continue;
         const int r = id / R1, k1 = id % R1;
-        const int o = (k1 / NB) * BLK + r * LDB + (R2 + 1) * (k1 % NB);
+        const int b = k1 / NB, cc0 = R2 * (k1 % NB);
 #pragma unroll
-        for (int i = 0; i < R2; ++i) x[t][i] = wave[o + i];
-        Dft<R2, -1>::run(x[t]);
+        for (int i = 0; i < R2; ++i) x[t][i] = wave[slot(b, r, cc0 + i)];
       }
-      cluster_barrier();
+      // the DFTs consume every loaded value, so the loads have completed
+      // before this thread arrives: the partner may then overwrite them
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) Dft<R2, -1>::run(x[t]);
+      cluster_arrive_relaxed();
+      cluster_wait();
       const uint32_t w0 = smem_u32(wave);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
         const int id = threadIdx.x + t * T;
+        if (TC % T != 0 && id >= TC) continue;
         const int r = id / R1, k1 = id % R1;
-        const int o = rank * BLK + r * LDB + (R2 + 1) * (k1 % NB);
-        const uint32_t dst = cluster_map(w0 + 8u * (uint32_t)o, (uint32_t)(k1 / NB));
+        const int b = k1 / NB, cc0 = R2 * (k1 % NB);
+        if (b == rank) {
 #pragma unroll
-        for (int i = 0; i < R2; ++i) st_cluster(dst + 8u * i, x[t][i]);
+          for (int i = 0; i < R2; ++i) wave[slot(rank, r, cc0 + i)] = x[t][i];
+        } else {
+          const uint32_t base = cluster_map(w0, (uint32_t)b);
+#pragma unroll
+          for (int i = 0; i < R2; ++i) st_cluster(base + 8u * (uint32_t)slot(rank, r, cc0 + i), x[t][i]);
+        }
       }
-      cluster_barrier();
+      cluster_arrive_release();
+      cluster_wait();
     } else {
 #pragma unroll 1
       for (int t = 0; t < CPT; ++t) {
         const int id = threadIdx.x + t * T;
+        if (TC % T != 0 && id >= TC) break;
         const int r = id / R1, k1 = id % R1;
-        const int o = (k1 / NB) * BLK + r * LDB + (R2 + 1) * (k1 % NB);
+        const int b = k1 / NB, cc0 = R2 * (k1 % NB);
         float2 x[R2];
 #pragma unroll
-        for (int i = 0; i < R2; ++i) x[i] = wave[o + i];
+        for (int i = 0; i < R2; ++i) x[i] = wave[slot(b, r, cc0 + i)];
         Dft<R2, DIR>::run(x);
         if constexpr (DIR > 0) {
 #pragma unroll
           for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
         }
 #pragma unroll
-        for (int i = 0; i < R2; ++i) wave[o + i] = x[i];
+        for (int i = 0; i < R2; ++i) wave[slot(b, r, cc0 + i)] = x[i];
       }
       __syncthreads();
     }
@@ -208,36 +250,42 @@ struct Tile {
 #pragma unroll
       for (int t = 0; t < SPT; ++t) {
         const int id = threadIdx.x + t * T;
+        if (TS % T != 0 && id >= TS) continue;
         const int n2 = id / ROWS, cc = id % ROWS;
-        const int base = n2 * LDB + phys(cc);
 #pragma unroll
-        for (int i = 0; i < R1; ++i) x[t][i] = wave[base + cs_off(i)];
-        Dft<R1, +1>::run(x[t]);
+        for (int i = 0; i < R1; ++i) x[t][i] = wave[slot(i / NB, n2 + R2 * (i % NB), cc)];
       }
-      cluster_barrier();
+#pragma unroll
+      for (int t = 0; t < SPT; ++t) Dft<R1, +1>::run(x[t]);
+      cluster_arrive_relaxed();
+      cluster_wait();
       const uint32_t w0 = smem_u32(wave);
+      uint32_t base[G];
+#pragma unroll
+      for (int b = 0; b < G; ++b) base[b] = cluster_map(w0, (uint32_t)b);
 #pragma unroll
       for (int t = 0; t < SPT; ++t) {
         const int id = threadIdx.x + t * T;
+        if (TS % T != 0 && id >= TS) continue;
         const int n2 = id / ROWS, cc = id % ROWS;
-        const int base = rank * BLK + n2 * LDB + phys(cc);
 #pragma unroll
         for (int i = 0; i < R1; ++i) {
-          const uint32_t dst = cluster_map(w0 + 8u * (uint32_t)(base + R2 * (i % NB) * LDB),
-                                           (uint32_t)(i / NB));
-          st_cluster(dst, x[t][i]);
+          const int b = i / NB, r = n2 + R2 * (i % NB);
+          if (b == rank) wave[slot(rank, r, cc)] = x[t][i];
+          else st_cluster(base[b] + 8u * (uint32_t)slot(rank, r, cc), x[t][i]);
         }
       }
-      cluster_barrier();
+      cluster_arrive_release();
+      cluster_wait();
     } else {
 #pragma unroll 1
       for (int t = 0; t < SPT; ++t) {
         const int id = threadIdx.x + t * T;
+        if (TS % T != 0 && id >= TS) break;
         const int n2 = id / ROWS, cc = id % ROWS;
-        const int base = n2 * LDB + phys(cc);
         float2 x[R1];
 #pragma unroll
-        for (int i = 0; i < R1; ++i) x[i] = wave[base + cs_off(i)];
+        for (int i = 0; i < R1; ++i) x[i] = wave[slot(i / NB, n2 + R2 * (i % NB), cc)];
         if constexpr (DIR < 0) {
           Dft<R1, -1>::run(x);
 #pragma unroll
@@ -246,7 +294,7 @@ struct Tile {
           Dft<R1, +1>::run(x);
         }
 #pragma unroll
-        for (int i = 0; i < R1; ++i) wave[base + cs_off(i)] = x[i];
+        for (int i = 0; i < R1; ++i) wave[slot(i / NB, n2 + R2 * (i % NB), cc)] = x[i];
       }
       __syncthreads();
     }
@@ -256,20 +304,22 @@ struct Tile {
   // (FROM_SMEM) or load(pu, pv); FWD applies the forward s2 so that register
   // i holds spectral slot pu = R2 k1 + i; op(pu, pv, v) is the pointwise
   // product; INV applies inverse s2' + twiddle and writes back in place.
+  // The caller synchronises.
   template <bool FROM_SMEM, bool FWD, bool INV, class Load, class Op>
   __device__ static void col_contig(float2* wave, const float2* twC, int rank, const Load& load,
                                     const Op& op) {
 #pragma unroll 1
     for (int t = 0; t < CPT; ++t) {
       const int id = threadIdx.x + t * T;
+      if (TC % T != 0 && id >= TC) break;
       const int k1 = id / ROWS, cc = id % ROWS;
-      const int base = (k1 / NB) * BLK + R2 * (k1 % NB) * LDB + phys(cc);
+      const int b = k1 / NB, r0 = R2 * (k1 % NB);
       const int pv = rank * ROWS + cc;
       const int pu0 = R2 * k1;
       float2 x[R2];
       if constexpr (FROM_SMEM) {
 #pragma unroll
-        for (int i = 0; i < R2; ++i) x[i] = wave[base + i * LDB];
+        for (int i = 0; i < R2; ++i) x[i] = wave[slot(b, r0 + i, cc)];
       } else {
 #pragma unroll
         for (int i = 0; i < R2; ++i) x[i] = load(pu0 + i, pv);
@@ -282,7 +332,7 @@ struct Tile {
 #pragma unroll
         for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
 #pragma unroll
-        for (int i = 0; i < R2; ++i) wave[base + i * LDB] = x[i];
+        for (int i = 0; i < R2; ++i) wave[slot(b, r0 + i, cc)] = x[i];
       }
     }
   }

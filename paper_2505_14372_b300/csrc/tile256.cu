@@ -2,6 +2,6 @@
 #include "engine_impl.cuh"
 
 namespace ptycho {
-using Tile256 = Tile<256, 4, 16, 16, 512, 1>;
+using Tile256 = Tile<256, 4, 16, 512, 1>;
 const EngineOps* engine_256() { return Engine<Tile256>::ops(); }
 }  // namespace ptycho
