@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Throughput of the batched mixed-state multislice forward + adjoint.
+
+One step = one gradient-descent iteration (ptycho_step) over one group of
+scan positions: probe spectra, forward model through every slice, noise-model
+loss, adjoint with the per-slice entry waves recomputed, object/probe
+gradient reduction and the Adam update (arXiv 2505.14372 §3, §3.1, §3.2).
+
+Default workload: 20 slices x 8 incoherent modes, 192x192 window,
+1024x1024 object, 128x128 raster scan (16384 positions), groups of 512,
+Poisson noise model, entry waves recomputed in the backward pass.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--workload 1|2|3] [--waves recompute|store] [--no-baseline]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica on its own GPU (the path has no exchange step), timing is the max over
+ranks, and `value` counts the positions of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint probe-positions/s (multislice, mixed-state); p50/p99 serve latency"
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3])
+    ap.add_argument("--waves", default="recompute", choices=["recompute", "store"])
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps)")
+    ap.add_argument("--group", type=int, default=0,
+                    help="override the group size (small cases for profiling; not a bench line)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def workload_geometry(wl, waves):
+    from paper_2505_14372_b300 import Geometry
+    return Geometry(S=wl.S, K=wl.K, N=wl.N, H=wl.H, W=wl.W, dx=wl.dx, lam=wl.lam, dz=wl.dz,
+                    bandlimit=wl.bandlimit, loss={0: "amplitude", 1: "poisson"}[wl.loss],
+                    eps=wl.eps, c=wl.c, waves=waves)
+
+
+def config_dict(wl, waves):
+    return {"workload": wl.name, "slices": wl.S, "modes": wl.K, "window": wl.N, "object": [wl.H, wl.W],
+            "positions": wl.P, "group": wl.B, "loss": {0: "amplitude", 1: "poisson"}[wl.loss],
+            "waves": waves, "grouping": "sparse, reshuffled every pass",
+            "l2": "inputs larger than L2 (patterns %.1f GB, object %.0f MB) - no flush" % (
+                wl.P * wl.N * wl.N * 4 / 1e9, wl.S * wl.H * wl.W * 8 / 1e6)}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2505_14372_b300", "csrc")
+    for name in ("radix.cuh", "tile.cuh", "kernels.cuh", "elementwise.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def fft_flops(NP):
+    return 5.0 * NP * math.log2(NP)
+
+
+def adjoint_algorithmic_flops(wl, items, recompute):
+    """Algorithmic FLOPs of one adjoint-kernel launch over `items` (position,
+    mode) pairs: 5 NP log2 NP per 2-D FFT (2S for the backward chain, plus 2S
+    for the forward recomputed inside it) and 6 per complex product of the
+    pointwise steps."""
+    NP = wl.N * wl.N
+    S = wl.S
+    ffts = (2 * S if recompute else 0) + 2 * S
+    # pointwise complex products per element: forward recompute: shift ramp 2,
+    # transmission S, propagator 2(S-1), seed 1; backward: object gradient S,
+    # conj(O) S, propagator 2(S-1), probe ramp 2
+    prods = (2 + S + 2 * (S - 1) + 1 if recompute else 1) + S + S + 2 * (S - 1) + 2
+    return items * (ffts * fft_flops(NP) + prods * 6.0 * NP)
+
+
+def cpu_oracle_leg(wl, geom, pos_all_np, n_pos_sample, O_init, P_np, sample_note):
+    """Times the FP64 oracle's step on a bounded sample of the workload."""
+    import oracle as orc
+    og = orc.Geom(S=wl.S, K=wl.K, h=wl.N, w=wl.N, H=wl.H, W=wl.W, dx=wl.dx, lam=wl.lam, dz=wl.dz,
+                  bandlimit=wl.bandlimit, loss=wl.loss, eps=wl.eps, c=wl.c)
+    from paper_2505_14372_b300 import synth
+    idx = np.arange(n_pos_sample)
+    E = synth.cbed_like_patterns(wl, n_pos_sample)
+    O = O_init.astype(np.complex128)
+    P = P_np.astype(np.complex128)
+    z = np.zeros
+    t0 = time.perf_counter()
+    orc.step(O, P, z(O.shape, complex), z(O.shape), z(P.shape, complex), z(P.shape), 1,
+             pos_all_np[:n_pos_sample], E, idx, og, 1e-3, 1e-4)
+    dt = time.perf_counter() - t0
+    return {"value": n_pos_sample / dt, "unit": "positions/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": sample_note, "seconds": dt}
+
+
+def run_reference(args, wl, rank):
+    """Reference arm: the FP64 oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    from paper_2505_14372_b300 import synth
+    P_np = synth.probe_modes(wl)
+    pos = synth.raster_positions(wl).astype(np.float64)
+    O_init = np.ones((wl.S, wl.H, wl.W), np.complex64)
+    per_step = 2 if wl.S > 1 else 16
+    note = (f"{per_step} positions x {wl.K} modes x {wl.S} slices per step (all slices and modes of the "
+            f"workload, object {wl.H}x{wl.W}), FP64 dense-DFT oracle incl. Adam on the full object")
+    import oracle as orc
+    og = orc.Geom(S=wl.S, K=wl.K, h=wl.N, w=wl.N, H=wl.H, W=wl.W, dx=wl.dx, lam=wl.lam, dz=wl.dz,
+                  bandlimit=wl.bandlimit, loss=wl.loss, eps=wl.eps, c=wl.c)
+    E = synth.cbed_like_patterns(wl, per_step * (args.steps + args.warmup))
+    O = O_init.astype(np.complex128)
+    P = P_np.astype(np.complex128)
+    mO, vO = np.zeros_like(O), np.zeros(O.shape)
+    mP, vP = np.zeros_like(P), np.zeros(P.shape)
+    t = 0
+    elapsed = 0.0
+    for it in range(args.warmup + args.steps):
+        sl = slice(it * per_step, (it + 1) * per_step)
+        idx = np.arange(per_step)
+        t0 = time.perf_counter()
+        t += 1
+        O, P, mO, vO, mP, vP, _, _ = orc.step(O, P, mO, vO, mP, vP, t, pos[sl], E[sl], idx, og, 1e-3, 1e-4)
+        if it >= args.warmup:
+            elapsed += time.perf_counter() - t0
+    value = per_step * args.steps / elapsed
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "positions/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(wl, args.waves),
+            "cpu_baseline": {"value": value, "unit": "positions/s", "cores": cores, "kind": "oracle",
+                             "sample": note},
+            "e2e": {"value": value, "unit": "positions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    from paper_2505_14372_b300 import synth
+    wl = synth.WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    from paper_2505_14372_b300 import AdamState, Context, adam_opt, kernels_launched, make_groups
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    if args.group:
+        import dataclasses
+        wl = dataclasses.replace(wl, B=args.group)
+    geom = workload_geometry(wl, args.waves)
+    B = wl.B
+
+    # ---- inputs resident in HBM
+    P_np = synth.probe_modes(wl)
+    pos_np = synth.raster_positions(wl)
+    Pd = torch.from_numpy(P_np).to(dev)
+    Od = torch.ones((wl.S, wl.H, wl.W), dtype=torch.complex64, device=dev)
+    pos_d = torch.from_numpy(pos_np).to(dev)
+    Iexp_d = synth.cbed_like_patterns_device(wl, wl.P, device=dev)
+    ngroups = wl.P // B
+    order = []
+    for it in range(math.ceil((args.warmup + args.steps) / ngroups) + 1):
+        order.append(make_groups(wl.P, B, seed=1234 + rank, iteration=it, mode="sparse"))
+    order = np.concatenate(order)
+    idx_all = torch.from_numpy(order.astype(np.int32)).to(dev)
+
+    ctx = Context(geom, max_batch=B)
+    st = AdamState(geom, device=dev)
+    opt = adam_opt(lr_O=1e-3, lr_P=1e-4)
+    stats = torch.zeros(2, dtype=torch.float64, device=dev)
+
+    def group(i):
+        return idx_all[i * B:(i + 1) * B]
+
+    for i in range(args.warmup):
+        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, group(i), stats=stats)
+    torch.cuda.synchronize()
+    ctx.check_status()
+    if world > 1:
+        dist.barrier()
+    ctx.set_timing(True)
+    ctx.kernel_times(reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    k0 = kernels_launched()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(args.steps):
+        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, group(args.warmup + i), stats=stats)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = kernels_launched() - k0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ctx.check_status()
+    ktimes = ctx.kernel_times()
+    ctx.set_timing(False)
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t_max.item())
+    value = world * B * args.steps / (ms_max / 1e3)
+    loss_last = stats.tolist()
+
+    # ---- end to end through the C-ABI with host buffers (pinned), copies timed
+    e2e_steps = args.e2e_steps or args.steps
+    h_order = order[(args.warmup + args.steps) * B:][: e2e_steps * B]
+    if len(h_order) < e2e_steps * B:
+        h_order = make_groups(wl.P, B, seed=99, iteration=0, mode="sparse")[: e2e_steps * B]
+    sel = torch.from_numpy(h_order.astype(np.int64)).to(dev)
+    I_host = Iexp_d.index_select(0, sel).cpu().pin_memory()
+    pos_host = pos_d.index_select(0, sel).cpu().pin_memory()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        ctx.step_host(Od, Pd, st, opt, pos_host[i * B:(i + 1) * B], I_host[i * B:(i + 1) * B])
+    t_e2e = time.perf_counter() - t0
+    te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * B * e2e_steps / float(te.item()), "unit": "positions/s",
+           "h2d_bytes_per_step": B * 2 * 4 + B * wl.N * wl.N * 4, "d2h_bytes_per_step": 16,
+           "api": "ptycho_step_host (pinned host buffers)"}
+
+    # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dom]
+    peaks, peak_src = measured_peaks()
+    recompute = args.waves == "recompute"
+    if dom == "adjoint":
+        flops = adjoint_algorithmic_flops(wl, B * wl.K, recompute)
+    else:
+        flops = B * wl.K * 2 * wl.S * fft_flops(wl.N * wl.N)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tf = nsm * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    achieved = flops / (dom_ms / dom_n / 1e3) / 1e12
+    traffic_path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    traffic = None
+    if os.path.exists(traffic_path):
+        with open(traffic_path) as f:
+            tj = json.load(f)
+        key = f"{dom}/{args.workload}/{args.waves}"
+        # counters are only valid for the kernel source they were taken on
+        if key in tj and tj[key].get("kernel_source") == kernel_source_hash():
+            traffic = tj[key]["bytes_per_item"] * B * wl.K
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf, "traffic": traffic,
+                "peak_source": f"FP32 CUDA cores: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{peaks.get('sm_max_mhz', 2032.0):.0f} MHz ({peak_src} max SM clock)",
+                "ms_per_launch": dom_ms / dom_n,
+                "share_of_step": dom_ms / ms,
+                "kernels_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()}}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "positions/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(wl, args.waves), "roofline": roofline, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks, "last_stats": loss_last}
+        if world == 1 and not args.no_baseline:
+            n_s = 8 if wl.S > 1 else 64
+            line["cpu_baseline"] = cpu_oracle_leg(
+                wl, geom, pos_np.astype(np.float64), n_s, np.ones((wl.S, wl.H, wl.W), np.complex64), P_np,
+                f"one oracle step on {n_s} positions x {wl.K} modes x {wl.S} slices (full object, Adam included)")
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

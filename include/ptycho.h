@@ -256,6 +256,10 @@ int ptycho_wait(ptycho_server* srv, uint64_t ticket, double timeout_ms);
 int ptycho_release(ptycho_server* srv, uint64_t ticket);
 int ptycho_server_stats_get(ptycho_server* srv, ptycho_server_stats* out);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts and servers); a diagnostic for counting device work. */
+uint64_t ptycho_kernels_launched(void);
+
 const char* ptycho_last_error(void);
 const char* ptycho_version(void);
 

@@ -88,6 +88,7 @@ SIGNATURES = {
     "ptycho_wait": (I32, [P_, C.c_uint64, C.c_double]),
     "ptycho_release": (I32, [P_, C.c_uint64]),
     "ptycho_server_stats_get": (I32, [P_, C.POINTER(ServerStats)]),
+    "ptycho_kernels_launched": (C.c_uint64, []),
     "ptycho_last_error": (C.c_char_p, []),
     "ptycho_version": (C.c_char_p, []),
 }

@@ -224,5 +224,10 @@ def make_groups(P: int, B: int, seed: int, iteration: int, mode: str = "sparse",
     return out
 
 
+def kernels_launched() -> int:
+    """Kernels this library has launched in this process."""
+    return int(lib().ptycho_kernels_launched())
+
+
 def version() -> str:
     return lib().ptycho_version().decode()

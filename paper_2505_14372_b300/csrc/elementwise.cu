@@ -1,10 +1,18 @@
 // FP64 reductions and the complex Adam update (arXiv 2505.14372 §3.2).
 #include <algorithm>
+#include <atomic>
 
 #include "elementwise.cuh"
 #include "engine.h"
+#include "ptycho.h"
 
 namespace ptycho {
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 // Block partial sums of |g|^2 over a complex array (FP64).
 __global__ void __launch_bounds__(kRedThreads) k_sumsq(const float2* __restrict__ g, long long n,
@@ -59,12 +67,14 @@ __global__ void k_adam(float2* __restrict__ z, float2* __restrict__ m, float* __
 
 
 cudaError_t launch_sumsq(const float2* g, long long n, double* partials, int nblocks, cudaStream_t s) {
+  count_launch();
   k_sumsq<<<nblocks, kRedThreads, 0, s>>>(g, n, partials);
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out, int sqrt_second,
                             cudaStream_t s) {
+  count_launch();
   k_finalize<<<1, kRedThreads, 0, s>>>(partials, n0, n1, out, sqrt_second);
   return cudaGetLastError();
 }
@@ -73,8 +83,11 @@ cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long lo
                         float b2, float eps, float bc1, float bc2, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+  count_launch();
   k_adam<<<blocks, 256, 0, s>>>(z, m, v, g, n, lr, b1, b2, eps, bc1, bc2);
   return cudaGetLastError();
 }
 
 }  // namespace ptycho
+
+extern "C" uint64_t ptycho_kernels_launched(void) { return ptycho::launches_so_far(); }

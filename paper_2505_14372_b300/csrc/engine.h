@@ -44,6 +44,10 @@ cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out,
 cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long long n, float lr, float b1,
                         float b2, float eps, float bc1, float bc2, cudaStream_t s);
 
+// process-wide count of kernels this library has launched (engine_impl /
+// elementwise launchers bump it once per launch)
+void count_launch();
+
 constexpr int kLossBlocks = 1184;  // 148 SMs x 8 resident reduction blocks
 constexpr int kNormBlocks = 592;
 

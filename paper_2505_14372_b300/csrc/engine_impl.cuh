@@ -26,6 +26,7 @@ struct Engine {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = TL::G > 1 ? 1 : 0;
+    count_launch();
     return cudaLaunchKernelEx(&cfg, kernel, args...);
   }
 
@@ -85,17 +86,20 @@ struct Engine {
   static cudaError_t modesum(const float2* A, float* I, int B, int K, cudaStream_t s) {
     const long long n = (long long)B * TL::NP;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+    count_launch();
     k_modesum<TL><<<blocks, 256, 0, s>>>(A, I, B, K);
     return cudaGetLastError();
   }
   static cudaError_t loss(const float2* A, const float* Iexp, const int* idx, int npos, int B, int K, int model,
                           float eps, float c, float* w, double* partials, int nblocks, cudaStream_t s) {
+    count_launch();
     k_loss<TL><<<nblocks, kRedThreads, 0, s>>>(A, Iexp, idx, npos, B, K, model, eps, c, w, partials);
     return cudaGetLastError();
   }
   static cudaError_t seed(const float* gI, int B, float* w, cudaStream_t s) {
     const long long n = (long long)B * TL::NP;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+    count_launch();
     k_seed<TL><<<blocks, 256, 0, s>>>(gI, B, w);
     return cudaGetLastError();
   }

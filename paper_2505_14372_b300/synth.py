@@ -230,3 +230,26 @@ def small_workload(cid=101, S=2, K=2, N=8, H=12, W=12, scan=(2, 2), step_px=2.0,
                     dose=dose, alpha_mrad=400.0, defocus_A=5.0, C3_A=0.0,
                     weights=tuple([1.0 / K] * K), dz_A=dz_A, dx=0.1,
                     bandlimit=bandlimit, atoms_per_slice=atoms)
+
+
+def cbed_like_patterns_device(wl: Workload, count: int, device="cuda", chunk=1024):
+    """float32 [count, N, N] Poisson patterns drawn on a CUDA device with torch
+    (same recipe as cbed_like_patterns; used for full-size workloads, where
+    drawing millions of counts on the host would take minutes)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(1000 * wl.cid + ROLE_PATTERN)
+    base = torch.from_numpy(cbed_like_rate(wl)).to(device=device, dtype=torch.float32)
+    f = torch.from_numpy(_freq(wl.N) / wl.N).to(device=device, dtype=torch.float32)
+    corr = wl.N / 12
+    g = torch.exp(-2.0 * (math.pi * corr) ** 2 * (f[:, None] ** 2 + f[None, :] ** 2))
+    out = torch.empty((count, wl.N, wl.N), dtype=torch.float32, device=device)
+    for i0 in range(0, count, chunk):
+        n = min(chunk, count - i0)
+        noise = torch.randn((n, wl.N, wl.N), generator=gen, device=device)
+        x = torch.fft.ifft2(torch.fft.fft2(noise) * g).real
+        x = x - x.mean(dim=(1, 2), keepdim=True)
+        x = x / (x.std(dim=(1, 2), keepdim=True) + 1e-30)
+        rate = torch.clamp(base * (1.0 + 0.25 * x), min=0.0)
+        out[i0:i0 + n] = torch.poisson(rate, generator=gen)
+    return out
