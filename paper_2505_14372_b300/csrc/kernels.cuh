@@ -234,6 +234,9 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_forward(const __grid_consta
   constexpr int N = TL::N;
 #pragma unroll 1
   for (int item = cluster_id<TL>(); item < L.total; item += n_clusters<TL>()) {
+    // the partner CTAs must be done with the previous item before remote
+    // writes of this one can land in their exchange buffers
+    TL::sync_cluster();
     const ProblemDesc& D = find_desc(L, item);
     const ItemGeo g = item_geo<TL>(D, item);
     if (!g.ok) {
@@ -264,6 +267,9 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_consta
   constexpr int N = TL::N;
 #pragma unroll 1
   for (int item = cluster_id<TL>(); item < L.total; item += n_clusters<TL>()) {
+    // the partner CTAs must be done with the previous item before remote
+    // writes of this one can land in their exchange buffers
+    TL::sync_cluster();
     const ProblemDesc& D = find_desc(L, item);
     const ItemGeo g = item_geo<TL>(D, item);
     if (!g.ok) {
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_spectrum(const float2
   for (int k = cluster_id<TL>(); k < K; k += n_clusters<TL>()) {
     const float2* Pk = P + (size_t)k * TL::NP;
     float2* out = Phat + (size_t)k * TL::NP;
-    __syncthreads();
+    TL::sync_cluster();
     TL::template row_strided<false, true>(sm.wave, sm.twS, rank,
                                           [&](int r, int c) { return Pk[r * N + c]; }, NoPre{}, NoOp4{});
     __syncthreads();
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_grad(const float2* __
   for (int k = cluster_id<TL>(); k < K; k += n_clusters<TL>()) {
     const float2* src = gPhat + (size_t)k * TL::NP;
     float2* out = gP + (size_t)k * TL::NP;
-    __syncthreads();
+    TL::sync_cluster();
     TL::template col_contig<false, false, true>(sm.wave, sm.twC, rank,
                                                 [&](int pu, int pv) { return src[pu * N + pv]; }, NoOp{});
     __syncthreads();
@@ -359,7 +365,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_fft_debug(const float2* __r
   for (int b = cluster_id<TL>(); b < count; b += n_clusters<TL>()) {
     const float2* x = in + (size_t)b * TL::NP;
     float2* y = out + (size_t)b * TL::NP;
-    __syncthreads();
+    TL::sync_cluster();
     if (dir < 0) {
       TL::template row_strided<false, true>(sm.wave, sm.twS, rank, [&](int r, int c) { return x[r * N + c]; },
                                             NoPre{}, NoOp4{});

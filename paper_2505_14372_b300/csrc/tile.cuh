@@ -93,7 +93,12 @@ struct Tile {
   static constexpr int ROWS = N / G;
   static constexpr int NB = ROWS / R2;               // R2-groups per block row
   static constexpr int BLK = ROWS * ROWS;
-  static constexpr int WAVE = G * BLK;               // float2 slots per CTA
+  // G == 2: the off-diagonal block is double-buffered (XA holds it in the
+  // row layout, XB in the column layout), so a layout switch writes into the
+  // partner's idle buffer and needs one cluster barrier and no register
+  // staging.  G == 4 keeps one slot per block and stages in registers.
+  static constexpr bool XB = (G == 2);
+  static constexpr int WAVE = XB ? 3 * BLK : G * BLK;  // float2 slots per CTA
   static constexpr int TS = ROWS * R2;               // strided-stage tasks (R1 elements)
   static constexpr int TC = ROWS * R1;               // contiguous-stage tasks (R2 elements)
   static constexpr int SPT = (TS + T - 1) / T;       // strided tasks per thread (last may idle)
@@ -110,11 +115,29 @@ struct Tile {
   // signed DFT frequency (fftfreq order) of natural bin n
   __host__ __device__ static constexpr int freq(int n) { return n < (N + 1) / 2 ? n : n - N; }
 
-  // swizzled slot of (block b, row r, column cc) within one CTA
-  __device__ static __forceinline__ int slot(int b, int r, int cc) {
+  // swizzled slot of (logical block b, row r, column cc) within one CTA, in
+  // the row layout (COL = false) or the column layout (COL = true)
+  template <bool COL>
+  __device__ static __forceinline__ int slot(int rank, int b, int r, int cc) {
     const int f = (R1 * r + NB * b + cc / R2) & 15;
-    return b * BLK + r * ROWS + (cc ^ f);
+    int base;
+    if constexpr (G == 1) base = 0;
+    else if constexpr (XB) base = b == rank ? 0 : (COL ? 2 * BLK : BLK);
+    else base = b * BLK;
+    return base + r * ROWS + (cc ^ f);
   }
+  // full barrier over the CTAs that share one wavefield
+  __device__ static void sync_cluster() {
+    if constexpr (G > 1) {
+      cluster_arrive_release();
+      cluster_wait();
+    } else {
+      __syncthreads();
+    }
+  }
+
+  __device__ static __forceinline__ int rslot(int rank, int b, int r, int cc) { return slot<false>(rank, b, r, cc); }
+  __device__ static __forceinline__ int cslot(int rank, int b, int r, int cc) { return slot<true>(rank, b, r, cc); }
 
   // Twiddles W_N^(n2 k1) = exp(-2 pi i n2 k1 / N): twS[k1*R2 + n2] (strided
   // stage, lanes over n2) and twC[n2*R1 + k1] (contiguous stage, lanes over
@@ -156,7 +179,7 @@ struct Tile {
 #pragma unroll
         for (int i = 0; i < R1; ++i) {
           const int col = n2 + R2 * i;
-          x[i] = wave[slot(col / ROWS, r, col % ROWS)];
+          x[i] = wave[rslot(rank, col / ROWS, r, col % ROWS)];
         }
         Dft<R1, +1>::run(x);
       } else {
@@ -172,7 +195,7 @@ struct Tile {
 #pragma unroll
         for (int i = 0; i < R1; ++i) {
           const int col = n2 + R2 * i;
-          wave[slot(col / ROWS, r, col % ROWS)] = x[i];
+          wave[rslot(rank, col / ROWS, r, col % ROWS)] = x[i];
         }
       }
     }
@@ -183,7 +206,7 @@ struct Tile {
   // place.  Ends with the barrier its result needs.
   template <int DIR>
   __device__ static void row_contig(float2* wave, const float2* twC, int rank) {
-    if constexpr (DIR < 0 && G > 1) {
+    if constexpr (DIR < 0 && G > 1 && !XB) {
       float2 x[CPT][R2];
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
@@ -192,7 +215,7 @@ struct Tile {
         const int r = id / R1, k1 = id % R1;
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
 #pragma unroll
-        for (int i = 0; i < R2; ++i) x[t][i] = wave[slot(b, r, cc0 + i)];
+        for (int i = 0; i < R2; ++i) x[t][i] = wave[rslot(rank, b, r, cc0 + i)];
       }
       // the DFTs consume every loaded value, so the loads have completed
       // before this thread arrives: the partner may then overwrite them
@@ -209,16 +232,17 @@ struct Tile {
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
         if (b == rank) {
 #pragma unroll
-          for (int i = 0; i < R2; ++i) wave[slot(rank, r, cc0 + i)] = x[t][i];
+          for (int i = 0; i < R2; ++i) wave[cslot(rank, rank, r, cc0 + i)] = x[t][i];
         } else {
           const uint32_t base = cluster_map(w0, (uint32_t)b);
 #pragma unroll
-          for (int i = 0; i < R2; ++i) st_cluster(base + 8u * (uint32_t)slot(rank, r, cc0 + i), x[t][i]);
+          for (int i = 0; i < R2; ++i) st_cluster(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + i), x[t][i]);
         }
       }
       cluster_arrive_release();
       cluster_wait();
     } else {
+      const uint32_t w0 = smem_u32(wave);
 #pragma unroll 1
       for (int t = 0; t < CPT; ++t) {
         const int id = threadIdx.x + t * T;
@@ -227,16 +251,29 @@ struct Tile {
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
         float2 x[R2];
 #pragma unroll
-        for (int i = 0; i < R2; ++i) x[i] = wave[slot(b, r, cc0 + i)];
+        for (int i = 0; i < R2; ++i) x[i] = wave[rslot(rank, b, r, cc0 + i)];
         Dft<R2, DIR>::run(x);
         if constexpr (DIR > 0) {
 #pragma unroll
           for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
         }
+        if (DIR > 0 || G == 1 || b == rank) {
+          // in place (row layout) or the diagonal block (same slots in both layouts)
 #pragma unroll
-        for (int i = 0; i < R2; ++i) wave[slot(b, r, cc0 + i)] = x[i];
+          for (int i = 0; i < R2; ++i) wave[rslot(rank, b, r, cc0 + i)] = x[i];
+        } else {
+          // off-diagonal block -> the partner's idle column-layout buffer
+          const uint32_t base = cluster_map(w0, (uint32_t)b);
+#pragma unroll
+          for (int i = 0; i < R2; ++i) st_cluster(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + i), x[i]);
+        }
       }
-      __syncthreads();
+      if constexpr (DIR < 0 && G > 1) {
+        cluster_arrive_release();
+        cluster_wait();
+      } else {
+        __syncthreads();
+      }
     }
   }
 
@@ -245,7 +282,7 @@ struct Tile {
   // block transpose when G > 1).  Ends with the barrier its result needs.
   template <int DIR>
   __device__ static void col_strided(float2* wave, const float2* twS, int rank) {
-    if constexpr (DIR > 0 && G > 1) {
+    if constexpr (DIR > 0 && G > 1 && !XB) {
       float2 x[SPT][R1];
 #pragma unroll
       for (int t = 0; t < SPT; ++t) {
@@ -253,7 +290,7 @@ struct Tile {
         if (TS % T != 0 && id >= TS) continue;
         const int n2 = id / ROWS, cc = id % ROWS;
 #pragma unroll
-        for (int i = 0; i < R1; ++i) x[t][i] = wave[slot(i / NB, n2 + R2 * (i % NB), cc)];
+        for (int i = 0; i < R1; ++i) x[t][i] = wave[cslot(rank, i / NB, n2 + R2 * (i % NB), cc)];
       }
 #pragma unroll
       for (int t = 0; t < SPT; ++t) Dft<R1, +1>::run(x[t]);
@@ -271,13 +308,19 @@ struct Tile {
 #pragma unroll
         for (int i = 0; i < R1; ++i) {
           const int b = i / NB, r = n2 + R2 * (i % NB);
-          if (b == rank) wave[slot(rank, r, cc)] = x[t][i];
-          else st_cluster(base[b] + 8u * (uint32_t)slot(rank, r, cc), x[t][i]);
+          if (b == rank) wave[rslot(rank, rank, r, cc)] = x[t][i];
+          else st_cluster(base[b] + 8u * (uint32_t)rslot(b, rank, r, cc), x[t][i]);
         }
       }
       cluster_arrive_release();
       cluster_wait();
     } else {
+      const uint32_t w0 = smem_u32(wave);
+      uint32_t base[G];
+      if constexpr (DIR > 0 && XB) {
+#pragma unroll
+        for (int b = 0; b < G; ++b) base[b] = cluster_map(w0, (uint32_t)b);
+      }
 #pragma unroll 1
       for (int t = 0; t < SPT; ++t) {
         const int id = threadIdx.x + t * T;
@@ -285,18 +328,29 @@ struct Tile {
         const int n2 = id / ROWS, cc = id % ROWS;
         float2 x[R1];
 #pragma unroll
-        for (int i = 0; i < R1; ++i) x[i] = wave[slot(i / NB, n2 + R2 * (i % NB), cc)];
+        for (int i = 0; i < R1; ++i) x[i] = wave[cslot(rank, i / NB, n2 + R2 * (i % NB), cc)];
         if constexpr (DIR < 0) {
           Dft<R1, -1>::run(x);
 #pragma unroll
           for (int k = 1; k < R1; ++k) x[k] = cmul(x[k], twS[k * R2 + n2]);
+#pragma unroll
+          for (int i = 0; i < R1; ++i) wave[cslot(rank, i / NB, n2 + R2 * (i % NB), cc)] = x[i];
         } else {
           Dft<R1, +1>::run(x);
-        }
 #pragma unroll
-        for (int i = 0; i < R1; ++i) wave[slot(i / NB, n2 + R2 * (i % NB), cc)] = x[i];
+          for (int i = 0; i < R1; ++i) {
+            const int b = i / NB, r = n2 + R2 * (i % NB);
+            if (G == 1 || b == rank) wave[rslot(rank, b, r, cc)] = x[i];
+            else st_cluster(base[b] + 8u * (uint32_t)rslot(b, rank, r, cc), x[i]);  // partner's idle buffer
+          }
+        }
       }
-      __syncthreads();
+      if constexpr (DIR > 0 && G > 1) {
+        cluster_arrive_release();
+        cluster_wait();
+      } else {
+        __syncthreads();
+      }
     }
   }
 
@@ -319,7 +373,7 @@ struct Tile {
       float2 x[R2];
       if constexpr (FROM_SMEM) {
 #pragma unroll
-        for (int i = 0; i < R2; ++i) x[i] = wave[slot(b, r0 + i, cc)];
+        for (int i = 0; i < R2; ++i) x[i] = wave[cslot(rank, b, r0 + i, cc)];
       } else {
 #pragma unroll
         for (int i = 0; i < R2; ++i) x[i] = load(pu0 + i, pv);
@@ -332,7 +386,7 @@ struct Tile {
 #pragma unroll
         for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
 #pragma unroll
-        for (int i = 0; i < R2; ++i) wave[slot(b, r0 + i, cc)] = x[i];
+        for (int i = 0; i < R2; ++i) wave[cslot(rank, b, r0 + i, cc)] = x[i];
       }
     }
   }
