@@ -1,0 +1,98 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point the header declares, validates arguments on the host, and its host
+logic (grouping, scratch sizing) behaves."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2505_14372_b300 import _lib
+from paper_2505_14372_b300.api import Geometry, make_groups, scratch_bytes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ptycho.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ptycho_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = C.CDLL(_lib.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding declares a signature for each of them
+    assert not [n for n in names if n not in _lib.SIGNATURES]
+
+
+def test_version_and_error_channel():
+    lib = _lib.lib()
+    assert b"sm_103a" in lib.ptycho_version()
+    g = _lib.Geom(1, 1, 96, 96, 128, 128, 0.1, 0.0197, None, 0.66, 0, 1e-3, 0.0, 0)
+    h = C.c_void_p()
+    rc = lib.ptycho_create(C.byref(g), 4, 0, C.byref(h))
+    assert rc == _lib.EINVAL and not h.value
+    assert b"96" in lib.ptycho_last_error()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(S=0), dict(K=0), dict(N=100), dict(H=32), dict(dx=0.0), dict(lam=-1.0),
+    dict(loss="poisson", eps=0.0), dict(loss="amplitude", eps=0.0, c=0.0), dict(c=-1.0),
+])
+def test_geometry_validation(bad):
+    args = dict(S=2, K=2, N=64, H=80, W=80, dz=(10.0,), loss="amplitude", eps=1e-3, c=0.0)
+    args.update(bad)
+    if args["S"] != 2:
+        args["dz"] = tuple([10.0] * max(args["S"] - 1, 0))
+    geom = Geometry(**args)
+    g, _dz = geom.to_c()
+    h = C.c_void_p()
+    assert _lib.lib().ptycho_create(C.byref(g), 4, 0, C.byref(h)) == _lib.EINVAL
+
+
+def test_null_dz_rejected():
+    g = _lib.Geom(3, 1, 64, 64, 80, 80, 0.1, 0.0197, None, 0.66, 0, 1e-3, 0.0, 0)
+    h = C.c_void_p()
+    assert _lib.lib().ptycho_create(C.byref(g), 4, 0, C.byref(h)) == _lib.EINVAL
+
+
+def test_null_context_calls_fail_cleanly():
+    lib = _lib.lib()
+    assert lib.ptycho_forward(None, None, None, None, 1, None, None) == _lib.EINVAL
+    assert lib.ptycho_check(None, None) == _lib.EINVAL
+    assert lib.ptycho_destroy(None) == _lib.OK
+
+
+def test_scratch_bytes_store_vs_recompute():
+    geom = Geometry(S=20, K=8, N=192, H=1024, W=1024, dz=tuple([10.0] * 19), loss="poisson", eps=0.8)
+    store = scratch_bytes(geom, 512, "store")
+    rec = scratch_bytes(geom, 512, "recompute")
+    waves = 512 * 8 * 20 * 192 * 192 * 8
+    assert store >= waves and rec < store - waves // 2
+
+
+@pytest.mark.parametrize("mode", ["sparse", "compact"])
+def test_groups_are_permutations_and_deterministic(mode):
+    pos = np.stack(np.meshgrid(np.arange(20) * 3.0, np.arange(25) * 3.0, indexing="ij"), -1).reshape(-1, 2)
+    P = len(pos)
+    a = make_groups(P, 64, seed=7, iteration=3, mode=mode, pos=pos)
+    b = make_groups(P, 64, seed=7, iteration=3, mode=mode, pos=pos)
+    c = make_groups(P, 64, seed=7, iteration=4, mode=mode, pos=pos)
+    assert np.array_equal(np.sort(a), np.arange(P))
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_compact_groups_are_spatially_compact():
+    pos = np.stack(np.meshgrid(np.arange(32) * 4.0, np.arange(32) * 4.0, indexing="ij"), -1).reshape(-1, 2)
+    P, B = len(pos), 64
+    comp = make_groups(P, B, seed=1, iteration=0, mode="compact", pos=pos)
+    sparse = make_groups(P, B, seed=1, iteration=0, mode="sparse", pos=pos)
+
+    def spread(order):
+        return np.mean([np.ptp(pos[order[i:i + B]], axis=0).sum() for i in range(0, P, B)])
+    assert spread(comp) < 0.5 * spread(sparse)
