@@ -215,6 +215,7 @@ typedef struct {
 #define PTYCHO_REQ_RUNNING 1
 #define PTYCHO_REQ_DONE 2
 #define PTYCHO_REQ_FAILED 3
+#define PTYCHO_REQ_ADMITTING 4   /* device state being allocated and uploaded */
 
 typedef struct {
   int32_t state;               /* PTYCHO_REQ_* */

@@ -200,6 +200,79 @@ class Context:
         return out
 
 
+STATE_NAMES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "admitting"}
+
+
+class Server:
+    """In-process continuous-batching server (ptycho_server_*): requests are
+    admitted against an HBM budget, keep their state on the device and have
+    their iterations batched into shared launches."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64):
+        h = C.c_void_p()
+        check(lib().ptycho_server_create(int(hbm_budget_bytes), int(max_active), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().ptycho_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, geom: Geometry, pos: np.ndarray, I_exp: np.ndarray, P_init: np.ndarray, O_init=None,
+               iterations: int = 1, batch: int = 64, grouping: str = "sparse", seed: int = 0, opt=None) -> int:
+        g, dz = geom.to_c()
+        pos = np.ascontiguousarray(pos, dtype=np.float32)
+        I_exp = np.ascontiguousarray(I_exp, dtype=np.float32)
+        P_init = np.ascontiguousarray(P_init, dtype=np.complex64)
+        O_ptr = None
+        if O_init is not None:
+            O_init = np.ascontiguousarray(O_init, dtype=np.complex64)
+            O_ptr = O_init.ctypes.data
+        req = _lib.Request(g, pos.shape[0], pos.ctypes.data, I_exp.ctypes.data, O_ptr, P_init.ctypes.data,
+                           iterations, batch, {"sparse": 0, "compact": 1}[grouping], seed,
+                           opt if opt is not None else adam_opt())
+        t = C.c_uint64()
+        check(lib().ptycho_submit(self.h, C.byref(req), C.byref(t)))  # copies the host arrays
+        return int(t.value)
+
+    def poll(self, ticket: int, geom: Geometry | None = None) -> dict:
+        st = _lib.Status()
+        res = _lib.Result()
+        check(lib().ptycho_poll(self.h, ticket, C.byref(st), C.byref(res)))
+        out = {"state": STATE_NAMES.get(st.state, st.state), "iterations_done": st.iterations_done,
+               "error": st.error, "last_loss": st.last_loss, "submit_ms": st.submit_ms,
+               "start_ms": st.start_ms, "finish_ms": st.finish_ms}
+        if st.state == 2:
+            out["loss"] = np.ctypeslib.as_array(res.loss, shape=(res.n_loss,)).copy() if res.n_loss else np.zeros(0)
+            out["iter_ms"] = np.ctypeslib.as_array(res.step_ms, shape=(res.n_step,)).copy() if res.n_step else np.zeros(0)
+            if geom is not None:
+                nO = geom.S * geom.H * geom.W
+                nP = geom.K * geom.N * geom.N
+                out["O"] = np.ctypeslib.as_array(C.cast(res.O, C.POINTER(C.c_float)), shape=(2 * nO,)).view(
+                    np.complex64).reshape(geom.S, geom.H, geom.W).copy()
+                out["P"] = np.ctypeslib.as_array(C.cast(res.P, C.POINTER(C.c_float)), shape=(2 * nP,)).view(
+                    np.complex64).reshape(geom.K, geom.N, geom.N).copy()
+        return out
+
+    def wait(self, ticket: int, timeout_ms: float = 600e3):
+        check(lib().ptycho_wait(self.h, ticket, float(timeout_ms)))
+
+    def release(self, ticket: int):
+        check(lib().ptycho_release(self.h, ticket))
+
+    def stats(self) -> dict:
+        s = _lib.ServerStats()
+        check(lib().ptycho_server_stats_get(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _lib.ServerStats._fields_}
+
+
 def scratch_bytes(geom: Geometry, B: int, waves: str = "store") -> int:
     g, _dz = geom.to_c()
     return int(lib().ptycho_scratch_bytes(C.byref(g), B, WAVES[waves]))

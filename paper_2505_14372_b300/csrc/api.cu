@@ -11,6 +11,7 @@
 
 #include "engine.h"
 #include "errors.h"
+#include "internal.h"
 #include "ptycho.h"
 
 using ptycho::EngineOps;
@@ -264,9 +265,11 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
 
 }  // namespace
 
-extern "C" {
-
-int ptycho_create(const ptycho_geom* geom, int32_t max_batch, size_t scratch_budget_bytes, ptycho_ctx** out) {
+// Context creation.  external_slots: the recompute scratch is supplied by
+// the caller of every launch (the server shares one per window size), so the
+// context holds none and always recomputes.
+static int create_impl(const ptycho_geom* geom, int32_t max_batch, size_t scratch_budget_bytes, bool external_slots,
+                       ptycho_ctx** out) {
   if (!out) return perr(PTYCHO_EINVAL, "out is NULL");
   *out = nullptr;
   int rc = validate_geom(geom);
@@ -296,8 +299,9 @@ int ptycho_create(const ptycho_geom* geom, int32_t max_batch, size_t scratch_bud
   c->res_adj = c->ops->resident_clusters(true, true);
   // waves mode
   const Layout Ls = make_layout(c->g, max_batch, true, 0);
-  const Layout Lr = make_layout(c->g, max_batch, false, c->slots);
-  if (geom->waves == PTYCHO_WAVES_STORE) c->store = true;
+  const Layout Lr = make_layout(c->g, max_batch, false, external_slots ? 0 : c->slots);
+  if (external_slots) c->store = false;
+  else if (geom->waves == PTYCHO_WAVES_STORE) c->store = true;
   else if (geom->waves == PTYCHO_WAVES_RECOMPUTE) c->store = false;
   else c->store = scratch_budget_bytes == 0 || Ls.total <= scratch_budget_bytes;
   const Layout& L = c->store ? Ls : Lr;
@@ -338,6 +342,12 @@ int ptycho_create(const ptycho_geom* geom, int32_t max_batch, size_t scratch_bud
   }
   *out = c;
   return PTYCHO_OK;
+}
+
+extern "C" {
+
+int ptycho_create(const ptycho_geom* geom, int32_t max_batch, size_t scratch_budget_bytes, ptycho_ctx** out) {
+  return create_impl(geom, max_batch, scratch_budget_bytes, false, out);
 }
 
 int ptycho_destroy(ptycho_ctx* c) {
@@ -560,3 +570,83 @@ int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, i
 const char* ptycho_version(void) { return "libptycho 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal API for the serving runtime (internal.h).
+namespace ptycho {
+
+int ctx_create_shared_slots(const ptycho_geom* geom, int max_batch, ptycho_ctx** out) {
+  return create_impl(geom, max_batch, 0, true, out);
+}
+
+size_t ctx_device_bytes(const ptycho_ctx* c) {
+  const size_t nO = (size_t)c->g.S * c->g.H * c->g.W;
+  return c->arena_bytes + nO * 8 + (size_t)c->g.K * c->NP * 8 + (c->g.S > 1 ? (size_t)(c->g.S - 1) * c->N * 8 : 0);
+}
+
+int resident_slots(int N) {
+  const EngineOps* ops = engine_for(N);
+  return ops ? ops->resident_clusters(true, false) : 0;
+}
+
+// One gradient step for several problems of the same window size: their
+// (position, mode) items share one forward launch and one adjoint launch.
+int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long slot_stride, unsigned* status,
+               cudaStream_t s) {
+  if (n < 1 || n > kMaxDesc) return perr(PTYCHO_EINVAL, "step_batch: 1..16 jobs");
+  const EngineOps* ops = jobs[0].c->ops;
+  LaunchArgs la{};
+  la.nd = n;
+  la.status = status;
+  la.slots = slots;
+  la.slot_stride = slot_stride;
+  int total = 0;
+  std::vector<Layout> L(n);
+  std::vector<int> nl(n);
+  for (int i = 0; i < n; ++i) {
+    const StepJob& J = jobs[i];
+    ptycho_ctx* c = J.c;
+    if (c->ops != ops || c->store) return perr(PTYCHO_EINVAL, "step_batch: mixed window sizes or stored waves");
+    if (J.B < 1 || J.B > c->max_batch) return perr(PTYCHO_EINVAL, "step_batch: bad group size");
+    if ((long long)c->g.S * c->NP > slot_stride) return perr(PTYCHO_EINVAL, "step_batch: slot too small");
+    L[i] = make_layout(c->g, c->max_batch, false, 0);
+    CK(ops->probe_spectrum(J.P, reinterpret_cast<float2*>(c->arena + L[i].Phat), c->g.K, s));
+    CK(cudaMemsetAsync(c->arena + L[i].gPhat, 0, (size_t)c->g.K * c->NP * 8, s));
+    CK(cudaMemsetAsync(c->gO, 0, (size_t)c->g.S * c->g.H * c->g.W * 8, s));
+    ProblemDesc d = base_desc(c, L[i], reinterpret_cast<const ptycho_c64*>(J.O), J.pos, J.idx, J.B, J.n_pos);
+    d.gO = c->gO;
+    d.item0 = total;
+    total += J.B * c->g.K;
+    la.d[i] = d;
+  }
+  la.total = total;
+  CK(ops->forward(la, std::min(total, jobs[0].c->res_fwd), false, s));
+  for (int i = 0; i < n; ++i) {
+    const StepJob& J = jobs[i];
+    ptycho_ctx* c = J.c;
+    nl[i] = (int)std::min<long long>(kLossBlocks, ((long long)J.B * c->NP + 255) / 256);
+    CK(ops->loss(la.d[i].A, J.Iexp, J.idx, J.n_pos, J.B, c->g.K, c->g.loss, (float)c->g.eps, (float)c->g.c,
+                 reinterpret_cast<float*>(c->arena + L[i].w), reinterpret_cast<double*>(c->arena + L[i].partials),
+                 nl[i], s));
+  }
+  CK(ops->adjoint(la, std::min(total, nslots), false, s));
+  for (int i = 0; i < n; ++i) {
+    const StepJob& J = jobs[i];
+    ptycho_ctx* c = J.c;
+    double* partials = reinterpret_cast<double*>(c->arena + L[i].partials);
+    const long long nO = (long long)c->g.S * c->g.H * c->g.W, nP = (long long)c->g.K * c->NP;
+    CK(ops->probe_grad(reinterpret_cast<float2*>(c->arena + L[i].gPhat), c->gP, c->g.K, 0, s));
+    CK(launch_sumsq(c->gO, nO, partials + nl[i], kNormBlocks, s));
+    CK(launch_sumsq(c->gP, nP, partials + nl[i] + kNormBlocks, kNormBlocks, s));
+    CK(launch_finalize(partials, nl[i], 2 * kNormBlocks, J.stats, 1, s));
+    const double t = (double)J.t;
+    const float bc1 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta1, t)));
+    const float bc2 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta2, t)));
+    CK(launch_adam(J.O, J.mO, J.vO, c->gO, nO, J.opt.lr_O, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s));
+    if (J.opt.update_probe)
+      CK(launch_adam(J.P, J.mP, J.vP, c->gP, nP, J.opt.lr_P, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s));
+  }
+  return PTYCHO_OK;
+}
+
+}  // namespace ptycho

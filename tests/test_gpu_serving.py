@@ -1,0 +1,107 @@
+"""Serving runtime (ptycho_submit / ptycho_poll): continuous batching of
+requests with different shapes, HBM admission, results equal alone and in
+the mix, and equal to the plain step path (arXiv 2505.14372 §2.3 job model,
+§3.2 solver)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from gpu_util import dev, host, problem, rel_l2
+from paper_2505_14372_b300 import AdamState, Context, PtychoError, Server, adam_opt, make_groups
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+def request(seed, S, K, N, H, W, n_pos, loss="poisson"):
+    geom, og, P, O, pos = problem(seed, S, K, N, H, W, n_pos, loss=loss, eps=0.8 if loss == "poisson" else 1e-3)
+    geom.waves = "recompute"
+    I_exp = np.random.default_rng(seed).poisson(orc.forward(O, P, pos, og) + 0.3).astype(np.float32)
+    return geom, P, pos, I_exp
+
+
+REQS = [
+    dict(seed=1, S=2, K=2, N=64, H=80, W=84, n_pos=30),
+    dict(seed=2, S=1, K=1, N=64, H=90, W=72, n_pos=21),
+    dict(seed=3, S=3, K=2, N=128, H=150, W=144, n_pos=10),
+    dict(seed=4, S=2, K=1, N=192, H=200, W=200, n_pos=6),
+]
+
+
+def run_alone(i, iters=3, batch=8):
+    r = request(**REQS[i])
+    srv = Server(8 * GB, 4)
+    t = srv.submit(r[0], r[2], r[3], r[1], iterations=iters, batch=batch, seed=11, opt=adam_opt(1e-2, 1e-3))
+    srv.wait(t)
+    out = srv.poll(t, r[0])
+    st = srv.stats()
+    srv.close()
+    return out, st
+
+
+def test_served_result_equals_plain_step_path():
+    geom, P, pos, I_exp = request(**REQS[0])
+    out, _ = run_alone(0)
+    assert out["state"] == "done" and out["iterations_done"] == 3
+    # plain path: same groups, same Adam steps, one ptycho_step per group
+    ctx = Context(geom, max_batch=8)
+    Od = torch.ones((geom.S, geom.H, geom.W), dtype=torch.complex64, device="cuda")
+    Pd = dev(P)
+    st = AdamState(geom)
+    opt = adam_opt(1e-2, 1e-3)
+    losses = []
+    for it in range(3):
+        perm = make_groups(len(pos), 8, seed=11, iteration=it, mode="sparse")
+        for g0 in range(0, len(pos), 8):
+            idx = dev(perm[g0:g0 + 8].astype(np.int32))
+            losses.append(float(ctx.step(Od, Pd, st, opt, dev(pos), dev(I_exp), idx)[0].item()))
+    assert rel_l2(out["O"], host(Od)) < 1e-4 and rel_l2(out["P"], host(Pd)) < 1e-4
+    assert np.allclose(out["loss"], losses, rtol=1e-4)
+
+
+def test_results_equal_alone_and_in_the_mix():
+    alone = [run_alone(i)[0] for i in range(len(REQS))]
+    srv = Server(16 * GB, 8)
+    reqs = [request(**q) for q in REQS]
+    tickets = [srv.submit(r[0], r[2], r[3], r[1], iterations=3, batch=8, seed=11, opt=adam_opt(1e-2, 1e-3))
+               for r in reqs]
+    for t in tickets:
+        srv.wait(t)
+    st = srv.stats()
+    assert st["finished"] == len(REQS) and st["failed"] == 0
+    assert st["p50_iter_ms"] > 0 and st["p99_iter_ms"] >= st["p50_iter_ms"] and st["positions_per_s"] > 0
+    for r, t, a in zip(reqs, tickets, alone):
+        o = srv.poll(t, r[0])
+        assert o["state"] == "done"
+        assert rel_l2(o["O"], a["O"]) < 1e-4 and rel_l2(o["P"], a["P"]) < 1e-4
+        assert np.allclose(o["loss"], a["loss"], rtol=1e-4)
+        srv.release(t)
+    with pytest.raises(PtychoError):
+        srv.poll(tickets[0])
+    srv.close()
+
+
+def test_admission_by_budget_and_rejection():
+    r = request(**REQS[2])
+    big = request(seed=9, S=2, K=1, N=128, H=140, W=140, n_pos=4)
+    tiny = Server(1 << 20, 2)   # 1 MiB cannot hold even the recompute scratch
+    with pytest.raises(PtychoError) as e:
+        tiny.submit(big[0], big[2], np.zeros((4, 128, 128), np.float32), big[1], iterations=1, batch=4)
+    assert e.value.code == -3
+    tiny.close()
+    # more requests than active slots: queued, admitted as slots free up
+    budget = 2 * GB
+    srv = Server(budget, 2)
+    tickets = [srv.submit(r[0], r[2], r[3], r[1], iterations=2, batch=5, seed=k) for k in range(5)]
+    peak = 0
+    while srv.stats()["finished"] < 5:
+        st = srv.stats()
+        peak = max(peak, st["admitted_bytes"])
+        assert st["admitted_bytes"] <= budget
+    for t in tickets:
+        srv.wait(t)
+    st = srv.stats()
+    assert st["finished"] == 5 and st["admitted"] == 5 and st["queue_depth"] == 0 and st["failed"] == 0
+    srv.close()
