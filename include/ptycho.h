@@ -127,6 +127,27 @@ int ptycho_adjoint(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, co
 int ptycho_vjp(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
                const float* gI, ptycho_c64* gO, ptycho_c64* gP, int32_t accumulate, ptycho_stream stream);
 
+/* Allocation-free forward model, for callers that cannot allocate device
+ * memory (a live-reconstruction loop that must not stall in cudaMalloc's
+ * locks and device synchronisation, an application that gives all device
+ * memory to its own pool, a plug-in whose host forbids allocating).  The
+ * paper has no counterpart: it is a packaging of ptycho_forward.
+ * Computes the same I_out[B][N][N] as ptycho_forward for the geometry *geom
+ * (copied per call; no context), using the kernels of ptycho_forward and a
+ * fixed 32 MiB scratch array that lives in the library (every GPU that loads
+ * the library holds it until exit).  The problem must fit it:
+ * K*N*N*8*(B+1) + (S-1)*N*8 plus a little alignment <= 32 MiB, else EINVAL
+ * with the sizes in the message.  Calls no cudaMalloc or cudaFree.  The first
+ * call on each device resolves the array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents; each call clears what must start at zero.  Calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * the shared scratch: order them.  Positions outside the object give zero
+ * intensity for their pattern. */
+int ptycho_forward_static(const ptycho_geom* geom, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
+                          int32_t B, float* I_out, ptycho_stream stream);
+
 /* Adam hyper-parameters (§3.2; Optax-style defaults 0.9, 0.999, 1e-8). */
 typedef struct {
   float lr_O, lr_P;
