@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--waves", default="recompute", choices=["recompute", "store"])
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mode: seeded Poisson arrivals of mixed-shape requests through ptycho_submit")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--iterations", type=int, default=2, help="iterations per served request")
+    ap.add_argument("--max-scan", type=int, default=48, help="largest scan side of a served request")
+    ap.add_argument("--rate", type=float, default=16.0, help="mean request arrivals per second")
     ap.add_argument("--group", type=int, default=0,
                     help="override the group size (small cases for profiling; not a bench line)")
     return ap.parse_args()
@@ -215,8 +221,101 @@ def run_reference(args, wl, rank):
     print(json.dumps(line), flush=True)
 
 
+def serve_requests(args):
+    """Seeded mixed-shape requests: scan side 32..max_scan at 3 px steps,
+    window 64/128/192/256, 1-30 slices, 1-8 modes, object = scan extent +
+    window + 4 px, Poisson-noise CBED-like patterns, Poisson arrival times."""
+    from paper_2505_14372_b300 import synth
+    rng = np.random.default_rng(5000)
+    out = []
+    t = 0.0
+    for i in range(args.requests):
+        t += rng.exponential(1.0 / args.rate)
+        n = int(rng.integers(32, args.max_scan + 1))
+        N = int(rng.choice([64, 128, 192, 256]))
+        S = int(rng.integers(1, 31))
+        K = int(rng.integers(1, 9))
+        side = (n - 1) * 3 + N + 4
+        wl = synth.Workload(5000 + i, f"served {i}", S=S, K=K, N=N, H=side, W=side, scan=(n, n), step_px=3.0,
+                            B=128, loss=1, eps=0.8, c=0.0, dose=5e4, alpha_mrad=24.0, defocus_A=50.0, C3_A=1e4,
+                            weights=tuple(np.exp(-np.arange(K)) / np.exp(-np.arange(K)).sum()))
+        out.append((t, wl))
+    return out
+
+
+def request_data(wl):
+    from paper_2505_14372_b300 import synth
+    P = synth.probe_modes(wl)
+    pos = synth.raster_positions(wl)
+    pool = synth.cbed_like_patterns(wl, 8)
+    I = np.ascontiguousarray(np.resize(pool, (wl.P, wl.N, wl.N)))
+    return P, pos, I
+
+
+def run_serve(args):
+    import threading
+    import torch
+    from paper_2505_14372_b300 import Server, adam_opt
+    torch.cuda.set_device(0)
+    reqs = serve_requests(args)
+    budget = 150 * (1 << 30)
+    opt = adam_opt(1e-3, 1e-4)
+
+    def submit(srv, wl):
+        P, pos, I = request_data(wl)
+        geom = workload_geometry(wl, "recompute")
+        return srv.submit(geom, pos, I, P, iterations=args.iterations, batch=wl.B, seed=wl.cid, opt=opt)
+
+    # continuous batching: requests arrive on their own schedule
+    srv = Server(budget, max_active=args.requests)
+    tickets = []
+    t0 = time.perf_counter()
+    for t_arr, wl in reqs:
+        dt = t_arr - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(submit(srv, wl))
+    for tk in tickets:
+        srv.wait(tk, 3600e3)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    positions = sum(wl.P * args.iterations for _, wl in reqs)
+    served = {"positions_per_s_wall": positions / wall, "positions_per_s_device": st["positions_per_s"],
+              "p50_iter_ms": st["p50_iter_ms"], "p99_iter_ms": st["p99_iter_ms"], "wall_s": wall,
+              "launches": st["launches"], "failed": st["failed"]}
+    srv.close()
+    # the same requests one at a time
+    srv = Server(budget, max_active=1)
+    t0 = time.perf_counter()
+    for _, wl in reqs:
+        tk = submit(srv, wl)
+        srv.wait(tk, 3600e3)
+    wall1 = time.perf_counter() - t0
+    st1 = srv.stats()
+    srv.close()
+    one = {"positions_per_s_wall": positions / wall1, "positions_per_s_device": st1["positions_per_s"],
+           "p50_iter_ms": st1["p50_iter_ms"], "p99_iter_ms": st1["p99_iter_ms"], "wall_s": wall1}
+    shapes = [(wl.P, wl.N, wl.S, wl.K) for _, wl in reqs]
+    line = {"metric": METRIC, "mode": "serve", "value": served["positions_per_s_wall"], "unit": "positions/s",
+            "p50_iter_ms": served["p50_iter_ms"], "p99_iter_ms": served["p99_iter_ms"], "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "served": served, "one_at_a_time": one,
+            "config": {"workload": "serving: Poisson arrivals of mixed-shape reconstruction requests",
+                       "requests": args.requests, "arrival_rate_per_s": args.rate,
+                       "iterations_per_request": args.iterations, "scan_sides": [32, args.max_scan],
+                       "windows": [64, 128, 192, 256], "slices": [1, 30], "modes": [1, 8], "group": 128,
+                       "hbm_budget_GB": 150, "positions_total": positions,
+                       "scaled_from": "50 iterations and scans up to 128x128 per request (reduced so one run "
+                                      "takes minutes)",
+                       "shapes": shapes}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.serve:
+        return run_serve(args)
     from paper_2505_14372_b300 import synth
     wl = synth.WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
