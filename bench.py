@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3])
     ap.add_argument("--waves", default="recompute", choices=["recompute", "store"])
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--dft", default="fft", choices=["fft", "tf32x3", "bf16x3", "tf32"],
+                    help="DFT evaluation inside the tile (tensor-core variants: 192x192 window)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps)")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: seeded Poisson arrivals of mixed-shape requests through ptycho_submit")
@@ -117,15 +119,15 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def workload_geometry(wl, waves):
+def workload_geometry(wl, waves, dft="fft"):
     from paper_2505_14372_b300 import Geometry
     return Geometry(S=wl.S, K=wl.K, N=wl.N, H=wl.H, W=wl.W, dx=wl.dx, lam=wl.lam, dz=wl.dz,
                     bandlimit=wl.bandlimit, loss={0: "amplitude", 1: "poisson"}[wl.loss],
-                    eps=wl.eps, c=wl.c, waves=waves)
+                    eps=wl.eps, c=wl.c, waves=waves, dft=dft)
 
 
-def config_dict(wl, waves):
-    return {"workload": wl.name, "slices": wl.S, "modes": wl.K, "window": wl.N, "object": [wl.H, wl.W],
+def config_dict(wl, waves, dft="fft"):
+    return {"workload": wl.name, "dft": dft, "slices": wl.S, "modes": wl.K, "window": wl.N, "object": [wl.H, wl.W],
             "positions": wl.P, "group": wl.B, "loss": {0: "amplitude", 1: "poisson"}[wl.loss],
             "waves": waves, "grouping": "sparse, reshuffled every pass",
             "l2": "inputs larger than L2 (patterns %.1f GB, object %.0f MB) - no flush" % (
@@ -336,7 +338,7 @@ def main():
     if args.group:
         import dataclasses
         wl = dataclasses.replace(wl, B=args.group)
-    geom = workload_geometry(wl, args.waves)
+    geom = workload_geometry(wl, args.waves, args.dft)
     B = wl.B
 
     # ---- inputs resident in HBM
@@ -448,7 +450,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "positions/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_dict(wl, args.waves), "roofline": roofline, "e2e": e2e,
+                "config": config_dict(wl, args.waves, args.dft), "roofline": roofline, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "last_stats": loss_last}
         if world == 1 and not args.no_baseline:
             n_s = 8 if wl.S > 1 else 64

@@ -76,6 +76,13 @@ typedef enum { PTYCHO_LOSS_AMPLITUDE = 0, PTYCHO_LOSS_POISSON = 1 } ptycho_loss;
  * AUTO stores when it fits the scratch budget. */
 typedef enum { PTYCHO_WAVES_AUTO = 0, PTYCHO_WAVES_STORE = 1, PTYCHO_WAVES_RECOMPUTE = 2 } ptycho_waves;
 
+/* Evaluation of the small DFTs inside the shared-memory FFT tile: radix
+ * butterflies on the FP32 CUDA cores (the default), or dense DFT-matrix
+ * products on the tensor cores with the FP32 operands split into two tf32 or
+ * bf16 terms (three products, near-FP32 accuracy) or a single tf32 product.
+ * The tensor-core variants exist for the 192 x 192 window. */
+typedef enum { PTYCHO_DFT_FFT = 0, PTYCHO_DFT_TF32X3 = 1, PTYCHO_DFT_BF16X3 = 2, PTYCHO_DFT_TF32 = 3 } ptycho_dft;
+
 /* Geometry and noise model of one reconstruction problem (§3, §3.1). */
 typedef struct {
   int32_t S, K;       /* slices, incoherent probe modes (K >= 1, S >= 1) */
@@ -90,6 +97,7 @@ typedef struct {
                          amplitude needs eps + c > 0 */
   double c;           /* amplitude-model offset (0 amplitude, 3/8 Anscombe) */
   int32_t waves;      /* ptycho_waves */
+  int32_t dft;        /* ptycho_dft: how the 2-D DFTs are evaluated */
 } ptycho_geom;
 
 typedef struct ptycho_ctx ptycho_ctx;

@@ -27,7 +27,7 @@ class Geom(C.Structure):
     _fields_ = [("S", C.c_int32), ("K", C.c_int32), ("h", C.c_int32), ("w", C.c_int32),
                 ("H", C.c_int32), ("W", C.c_int32), ("dx", C.c_double), ("lam", C.c_double),
                 ("dz", C.POINTER(C.c_double)), ("bandlimit", C.c_double), ("loss", C.c_int32),
-                ("eps", C.c_double), ("c", C.c_double), ("waves", C.c_int32)]
+                ("eps", C.c_double), ("c", C.c_double), ("waves", C.c_int32), ("dft", C.c_int32)]
 
 
 class Opt(C.Structure):

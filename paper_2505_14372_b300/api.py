@@ -17,6 +17,7 @@ from ._lib import check, lib
 
 LOSS = {"amplitude": 0, "anscombe": 0, "poisson": 1}
 WAVES = {"auto": 0, "store": 1, "recompute": 2}
+DFT = {"fft": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3}
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
@@ -49,12 +50,13 @@ class Geometry:
     eps: float = 1e-3
     c: float = 0.0
     waves: str = "auto"
+    dft: str = "fft"
 
     def to_c(self):
         dz = (C.c_double * max(len(self.dz), 1))(*self.dz) if len(self.dz) else None
         g = _lib.Geom(self.S, self.K, self.N, self.N, self.H, self.W, self.dx, self.lam,
                       C.cast(dz, C.POINTER(C.c_double)) if dz is not None else None,
-                      self.bandlimit, LOSS[self.loss], self.eps, self.c, WAVES[self.waves])
+                      self.bandlimit, LOSS[self.loss], self.eps, self.c, WAVES[self.waves], DFT[self.dft])
         return g, dz
 
 

@@ -55,6 +55,9 @@ int validate_geom(const ptycho_geom* g) {
   if (g->h != g->w) return perr(PTYCHO_EINVAL, "window must be square (h == w)");
   if (!ptycho::engine_for(g->h))
     return perr(PTYCHO_EINVAL, "window size " + std::to_string(g->h) + " not in {64, 128, 192, 256}");
+  if (g->dft < 0 || g->dft > 3) return perr(PTYCHO_EINVAL, "unknown dft mode");
+  if (g->dft != PTYCHO_DFT_FFT && !ptycho::engine_for(g->h, g->dft))
+    return perr(PTYCHO_EINVAL, "the tensor-core DFT variants are built for the 192 x 192 window only");
   if (g->H < g->h || g->W < g->w) return perr(PTYCHO_EINVAL, "object smaller than the window");
   if (!(g->dx > 0) || !(g->lambda > 0) || !std::isfinite(g->dx) || !std::isfinite(g->lambda))
     return perr(PTYCHO_EINVAL, "dx and lambda must be finite and > 0");
@@ -280,7 +283,7 @@ static int create_impl(const ptycho_geom* geom, int32_t max_batch, size_t scratc
   c->g = *geom;
   c->dz.assign(geom->dz ? geom->dz : nullptr, geom->dz ? geom->dz + std::max(geom->S - 1, 0) : nullptr);
   c->g.dz = c->dz.data();
-  c->ops = ptycho::engine_for(geom->h);
+  c->ops = ptycho::engine_for(geom->h, geom->dft);
   c->N = geom->h;
   c->NP = geom->h * geom->w;
   c->max_batch = max_batch;

@@ -27,7 +27,11 @@ const EngineOps* engine_128();
 const EngineOps* engine_192();
 const EngineOps* engine_256();
 
-inline const EngineOps* engine_for(int N) {
+// tensor-core DFT variants (mode 1 TF32x3, 2 BF16x3, 3 TF32x1), 192x192 only
+const EngineOps* engine_192_tc(int mode);
+
+inline const EngineOps* engine_for(int N, int dft = 0) {
+  if (dft != 0) return N == 192 ? engine_192_tc(dft) : nullptr;
   switch (N) {
     case 64: return engine_64();
     case 128: return engine_128();

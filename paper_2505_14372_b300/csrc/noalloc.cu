@@ -81,7 +81,7 @@ __global__ void k_static_chirp_table(float2* Hc, const double* dz_dev, int gaps,
 extern "C" int ptycho_forward_static(const ptycho_geom* g, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
                                      int32_t B, float* I_out, ptycho_stream stream) {
   if (!g) return perr(PTYCHO_EINVAL, "geometry is NULL");
-  const ptycho::EngineOps* ops = ptycho::engine_for(g->h);
+  const ptycho::EngineOps* ops = ptycho::engine_for(g->h, g->dft);
   if (!ops || g->h != g->w) return perr(PTYCHO_EINVAL, "window must be square with N in {64, 128, 192, 256}");
   if (g->S < 1 || g->K < 1 || g->H < g->h || g->W < g->w || !(g->dx > 0) || !(g->lambda > 0) ||
       (g->S > 1 && !g->dz))

@@ -470,6 +470,7 @@ int ptycho_submit(ptycho_server* s, const ptycho_request* q, uint64_t* ticket) {
   const ptycho_geom& g = q->geom;
   if (g.h != g.w || class_of(g.h) < 0) return perr(PTYCHO_EINVAL, "window must be 64, 128, 192 or 256 square");
   if (g.S < 1 || g.S > kMaxSlices) return perr(PTYCHO_EINVAL, "served requests need 1 <= S <= 32");
+  if (g.dft != PTYCHO_DFT_FFT) return perr(PTYCHO_EINVAL, "served requests use the FFT tile (dft = 0)");
   if (g.K < 1 || g.H < g.h || g.W < g.w || (g.S > 1 && !g.dz)) return perr(PTYCHO_EINVAL, "bad geometry");
   if (q->n_pos < 1 || !q->pos || !q->I_exp || !q->P_init || q->iterations < 1 || q->batch < 1)
     return perr(PTYCHO_EINVAL, "bad request (positions, patterns, probe, iterations, batch)");

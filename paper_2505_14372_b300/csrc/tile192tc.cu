@@ -1,0 +1,161 @@
+// Tensor-core DFT variant of the 192x192 tile (2-CTA cluster): TF32x3,
+// BF16x3 and TF32x1 modes.  Also builds the DFT-matrix fragment tables.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "engine_impl.cuh"
+#include "tile_tc.cuh"
+
+namespace ptycho {
+
+namespace {
+
+uint32_t f32_bits(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  return u;
+}
+float bits_f32(uint32_t u) {
+  float x;
+  std::memcpy(&x, &u, 4);
+  return x;
+}
+// round to tf32 (10 mantissa bits), nearest, ties away from zero
+float to_tf32(float x) {
+  uint32_t u = f32_bits(x);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  return bits_f32(u);
+}
+// round to bf16, nearest even
+uint16_t to_bf16(float x) {
+  const uint32_t u = f32_bits(x);
+  const uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(r >> 16);
+}
+float bf16_to_f32(uint16_t b) { return bits_f32((uint32_t)b << 16); }
+
+// Real 32 x 32 matrix of the complex R-point DFT (rows: real then imaginary
+// outputs, columns: real then imaginary inputs), zero beyond R.
+double dft_real(int R, int dir, int row, int col) {
+  const int m = row % 16, e = col % 16;
+  if (m >= R || e >= R) return 0.0;
+  const double a = 2.0 * M_PI * (double)((m * e) % R) / (double)R;
+  const double wr = std::cos(a), wi = dir * std::sin(a);
+  const bool out_im = row >= 16, in_im = col >= 16;
+  if (!out_im && !in_im) return wr;
+  if (!out_im && in_im) return -wi;
+  if (out_im && !in_im) return wi;
+  return wr;
+}
+
+void fill_table(int mode, int R, int dir, uint32_t* out) {
+  for (int lane = 0; lane < 32; ++lane) {
+    const int g = lane / 4, t = lane % 4;
+    uint32_t* o = out + lane * 64;
+    if (mode == TC_BF16X3) {
+      // m16n8k16 A fragment: {A[g][2t], A[g][2t+1]}, {A[g+8][..]}, {A[g][2t+8], ..}, {A[g+8][2t+8], ..}
+      for (int mt = 0; mt < 2; ++mt)
+        for (int ks = 0; ks < 2; ++ks)
+          for (int reg = 0; reg < 4; ++reg) {
+            const int row = 16 * mt + g + ((reg & 1) ? 8 : 0);
+            const int col = 16 * ks + 2 * t + ((reg & 2) ? 8 : 0);
+            uint32_t hi = 0, lo = 0;
+            for (int h = 0; h < 2; ++h) {
+              const double v = dft_real(R, dir, row, col + h);
+              const uint16_t bh = to_bf16((float)v);
+              const uint16_t bl = to_bf16((float)(v - (double)bf16_to_f32(bh)));
+              hi |= (uint32_t)bh << (16 * h);
+              lo |= (uint32_t)bl << (16 * h);
+            }
+            o[(mt * 2 + ks) * 4 + reg] = hi;
+            o[16 + (mt * 2 + ks) * 4 + reg] = lo;
+          }
+    } else {
+      // m16n8k8 A fragment: A[g][t], A[g+8][t], A[g][t+4], A[g+8][t+4]
+      for (int mt = 0; mt < 2; ++mt)
+        for (int kk = 0; kk < 4; ++kk)
+          for (int reg = 0; reg < 4; ++reg) {
+            const int row = 16 * mt + g + ((reg & 1) ? 8 : 0);
+            const int col = 8 * kk + t + ((reg & 2) ? 4 : 0);
+            const double v = dft_real(R, dir, row, col);
+            const float h = to_tf32((float)v);
+            const float l = to_tf32((float)(v - (double)h));
+            o[(mt * 4 + kk) * 4 + reg] = f32_bits(h);
+            o[32 + (mt * 4 + kk) * 4 + reg] = f32_bits(l);
+          }
+    }
+  }
+}
+
+std::mutex g_mu;
+bool g_ready[64] = {};
+
+// Fills the fragment tables on the current device once.
+cudaError_t ensure_tables(int R1, int R2) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (dev >= 0 && dev < 64 && g_ready[dev]) return cudaSuccess;
+  std::vector<uint32_t> h((size_t)3 * 4 * kTcTableWords, 0u);
+  const int modes[3] = {TC_TF32X3, TC_BF16X3, TC_TF32X1};
+  for (int mi = 0; mi < 3; ++mi)
+    for (int m = 0; m < 4; ++m)
+      fill_table(modes[mi], m < 2 ? R1 : R2, (m & 1) ? +1 : -1, &h[((size_t)mi * 4 + m) * kTcTableWords]);
+  e = cudaMemcpyToSymbol(g_tc_tables, h.data(), h.size() * 4);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) g_ready[dev] = true;
+  return e;
+}
+
+template <int MODE>
+struct TcEngine {
+  using TL = TileTC<Tile<192, 2, 16, 384, 1>, MODE>;
+  using E = Engine<TL>;
+  static cudaError_t probe_spectrum(const float2* P, float2* Phat, int K, cudaStream_t s) {
+    cudaError_t e = ensure_tables(TL::R1, TL::R2);
+    return e != cudaSuccess ? e : E::probe_spectrum(P, Phat, K, s);
+  }
+  static cudaError_t forward(const LaunchArgs& L, int clusters, bool store, cudaStream_t s) {
+    cudaError_t e = ensure_tables(TL::R1, TL::R2);
+    return e != cudaSuccess ? e : E::forward(L, clusters, store, s);
+  }
+  static cudaError_t adjoint(const LaunchArgs& L, int clusters, bool store, cudaStream_t s) {
+    cudaError_t e = ensure_tables(TL::R1, TL::R2);
+    return e != cudaSuccess ? e : E::adjoint(L, clusters, store, s);
+  }
+  static cudaError_t probe_grad(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s) {
+    cudaError_t e = ensure_tables(TL::R1, TL::R2);
+    return e != cudaSuccess ? e : E::probe_grad(gPhat, gP, K, acc, s);
+  }
+  static cudaError_t fft_debug(const float2* in, float2* out, int count, int dir, cudaStream_t s) {
+    cudaError_t e = ensure_tables(TL::R1, TL::R2);
+    return e != cudaSuccess ? e : E::fft_debug(in, out, count, dir, s);
+  }
+  static const EngineOps* ops() {
+    static const EngineOps o = [] {
+      EngineOps x = *E::ops();
+      x.probe_spectrum = &probe_spectrum;
+      x.forward = &forward;
+      x.adjoint = &adjoint;
+      x.probe_grad = &probe_grad;
+      x.fft_debug = &fft_debug;
+      return x;
+    }();
+    return &o;
+  }
+};
+
+}  // namespace
+
+const EngineOps* engine_192_tc(int mode) {
+  switch (mode) {
+    case TC_TF32X3: return TcEngine<TC_TF32X3>::ops();
+    case TC_BF16X3: return TcEngine<TC_BF16X3>::ops();
+    case TC_TF32X1: return TcEngine<TC_TF32X1>::ops();
+    default: return nullptr;
+  }
+}
+
+}  // namespace ptycho

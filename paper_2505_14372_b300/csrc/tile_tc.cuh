@@ -1,0 +1,230 @@
+// Tensor-core variant of the FFT tile: the same layouts, stages, fusions
+// and cluster exchange as Tile, with every R1- and R2-point DFT evaluated by
+// tc_dft8 (8 tasks per warp per call) instead of the register butterflies.
+// Exposes the interface the kernels use, so the forward/adjoint kernels are
+// instantiated unchanged on it.
+#pragma once
+#include "tc_dft.cuh"
+#include "tile.cuh"
+
+namespace ptycho {
+
+// A-fragment tables, [MODE-1][matrix][lane][reg]; matrix 0: R1 forward,
+// 1: R1 inverse, 2: R2 forward, 3: R2 inverse (filled once per device by the
+// host).  Defined here: only the tensor-core translation unit includes this.
+constexpr int kTcTableWords = 32 * 64;
+__device__ uint32_t g_tc_tables[3][4][kTcTableWords];
+
+template <class Base, int MODE>
+struct TileTC : Base {
+  using B_ = Base;
+  static constexpr int N = Base::N, G = Base::G, R1 = Base::R1, R2 = Base::R2, T = Base::T, MINB = Base::MINB;
+  static constexpr int NP = Base::NP, ROWS = Base::ROWS, NB = Base::NB, BLK = Base::BLK, WAVE = Base::WAVE;
+  static constexpr int TS = Base::TS, TC = Base::TC;
+  static constexpr size_t SMEM = Base::SMEM;
+  static constexpr bool XB = Base::XB;
+  static constexpr int WARPS = T / 32;
+  static_assert(G == 1 || XB, "tensor-core tile: single CTA or double-buffered exchange");
+  static_assert(TS % 8 == 0 && TC % 8 == 0 && R1 <= 16 && R2 <= 16, "8-task batches of <= 16-point DFTs");
+
+  using Base::cslot;
+  using Base::freq;
+  using Base::init_tables;
+  using Base::nat;
+  using Base::perm;
+  using Base::rslot;
+  using Base::sync_cluster;
+
+  __device__ static const uint32_t* table(int m) { return g_tc_tables[MODE - 1][m]; }
+  template <int R, int DIR>
+  __device__ static void load_mat(TcMat<MODE>& M) {
+    M.load(table((R == R1 && R1 != R2 ? 0 : 2) + (DIR > 0 ? 1 : 0)));
+  }
+
+  // ---- row strided ------------------------------------------------------
+  template <bool FROM_SMEM, bool TO_SMEM, class Load, class Pre, class Op>
+  __device__ static void row_strided(float2* wave, const float2* twS, int rank, const Load& load, const Pre& pre,
+                                     const Op& op) {
+    const int warp = threadIdx.x >> 5;
+    TcMat<MODE> Mi, Mf;
+    if constexpr (FROM_SMEM) load_mat<R1, +1>(Mi);
+    if constexpr (TO_SMEM) load_mat<R1, -1>(Mf);
+    auto sl = [&](int id, int e) {
+      const int r = id / R2, col = id % R2 + R2 * e;
+      return rslot(rank, col / ROWS, r, col % ROWS);
+    };
+#pragma unroll 1
+    for (int q = warp; q < TS / 8; q += WARPS) {
+      const int task0 = 8 * q;
+      if constexpr (FROM_SMEM) {
+        tc_dft8<MODE, R1>(
+            Mi, task0, [&](int id, int e) { return wave[sl(id, e)]; },
+            [&](int id, int m, float2 v) {
+              if constexpr (TO_SMEM) {
+                wave[sl(id, m)] = v;
+              } else {
+                const int r = id / R2, col = id % R2 + R2 * m;
+                const int grow = rank * ROWS + r;
+                op(grow, col, v, pre(grow, col));
+              }
+            });
+        if constexpr (TO_SMEM) __syncwarp();
+      }
+      if constexpr (TO_SMEM) {
+        tc_dft8<MODE, R1>(
+            Mf, task0,
+            [&](int id, int e) {
+              const int r = id / R2, col = id % R2 + R2 * e;
+              const int grow = rank * ROWS + r;
+              float2 v;
+              if constexpr (FROM_SMEM) v = wave[sl(id, e)];
+              else v = load(grow, col);
+              op(grow, col, v, pre(grow, col));
+              return v;
+            },
+            [&](int id, int k, float2 v) {
+              const int n2 = id % R2;
+              wave[sl(id, k)] = k ? cmul(v, twS[k * R2 + n2]) : v;
+            });
+      }
+    }
+  }
+
+  // ---- row contiguous ---------------------------------------------------
+  template <int DIR>
+  __device__ static void row_contig(float2* wave, const float2* twC, int rank) {
+    const int warp = threadIdx.x >> 5;
+    TcMat<MODE> M;
+    load_mat<R2, DIR>(M);
+    const uint32_t w0 = smem_u32(wave);
+    uint32_t base[G];
+#pragma unroll
+    for (int b = 0; b < G; ++b) base[b] = G > 1 ? cluster_map(w0, (uint32_t)b) : w0;
+    auto sl = [&](int id, int e) {
+      const int r = id / R1, k1 = id % R1;
+      return rslot(rank, k1 / NB, r, R2 * (k1 % NB) + e);
+    };
+#pragma unroll 1
+    for (int q = warp; q < TC / 8; q += WARPS) {
+      tc_dft8<MODE, R2>(
+          M, 8 * q, [&](int id, int e) { return wave[sl(id, e)]; },
+          [&](int id, int m, float2 v) {
+            const int r = id / R1, k1 = id % R1, b = k1 / NB;
+            if constexpr (DIR > 0) {
+              if (m) v = cmulc(v, twC[m * R1 + k1]);
+              wave[sl(id, m)] = v;
+            } else {
+              if (G == 1 || b == rank) wave[sl(id, m)] = v;
+              else st_cluster(base[b] + 8u * (uint32_t)cslot(b, rank, r, R2 * (k1 % NB) + m), v);
+            }
+          });
+    }
+    if constexpr (DIR < 0 && G > 1) {
+      cluster_arrive_release();
+      cluster_wait();
+    } else {
+      __syncthreads();
+    }
+  }
+
+  // ---- column strided ---------------------------------------------------
+  template <int DIR>
+  __device__ static void col_strided(float2* wave, const float2* twS, int rank) {
+    const int warp = threadIdx.x >> 5;
+    TcMat<MODE> M;
+    load_mat<R1, DIR>(M);
+    const uint32_t w0 = smem_u32(wave);
+    uint32_t base[G];
+#pragma unroll
+    for (int b = 0; b < G; ++b) base[b] = G > 1 ? cluster_map(w0, (uint32_t)b) : w0;
+    auto sl = [&](int id, int e) {
+      const int n2 = id / ROWS, cc = id % ROWS;
+      return cslot(rank, e / NB, n2 + R2 * (e % NB), cc);
+    };
+#pragma unroll 1
+    for (int q = warp; q < TS / 8; q += WARPS) {
+      tc_dft8<MODE, R1>(
+          M, 8 * q, [&](int id, int e) { return wave[sl(id, e)]; },
+          [&](int id, int m, float2 v) {
+            const int n2 = id / ROWS, cc = id % ROWS;
+            if constexpr (DIR < 0) {
+              wave[sl(id, m)] = m ? cmul(v, twS[m * R2 + n2]) : v;
+            } else {
+              const int b = m / NB, r = n2 + R2 * (m % NB);
+              if (G == 1 || b == rank) wave[rslot(rank, b, r, cc)] = v;
+              else st_cluster(base[b] + 8u * (uint32_t)rslot(b, rank, r, cc), v);
+            }
+          });
+    }
+    if constexpr (DIR > 0 && G > 1) {
+      cluster_arrive_release();
+      cluster_wait();
+    } else {
+      __syncthreads();
+    }
+  }
+
+  // ---- column contiguous (spectral side) --------------------------------
+  template <bool FROM_SMEM, bool FWD, bool INV, class Load, class Op>
+  __device__ static void col_contig(float2* wave, const float2* twC, int rank, const Load& load, const Op& op) {
+    const int warp = threadIdx.x >> 5;
+    TcMat<MODE> Mf, Mi;
+    if constexpr (FWD) load_mat<R2, -1>(Mf);
+    if constexpr (INV) load_mat<R2, +1>(Mi);
+    auto sl = [&](int id, int e) {
+      const int k1 = id / ROWS, cc = id % ROWS;
+      return cslot(rank, k1 / NB, R2 * (k1 % NB) + e, cc);
+    };
+    auto pu_pv = [&](int id, int e, int& pu, int& pv) {
+      const int k1 = id / ROWS, cc = id % ROWS;
+      pu = R2 * k1 + e;
+      pv = rank * ROWS + cc;
+    };
+#pragma unroll 1
+    for (int q = warp; q < TC / 8; q += WARPS) {
+      const int task0 = 8 * q;
+      if constexpr (FWD) {
+        tc_dft8<MODE, R2>(
+            Mf, task0, [&](int id, int e) { return wave[sl(id, e)]; },
+            [&](int id, int m, float2 v) {
+              if constexpr (INV) {
+                wave[sl(id, m)] = v;
+              } else {
+                int pu, pv;
+                pu_pv(id, m, pu, pv);
+                op(pu, pv, v);
+              }
+            });
+        if constexpr (INV) __syncwarp();
+      }
+      if constexpr (INV) {
+        tc_dft8<MODE, R2>(
+            Mi, task0,
+            [&](int id, int e) {
+              int pu, pv;
+              pu_pv(id, e, pu, pv);
+              float2 v;
+              if constexpr (FWD || FROM_SMEM) v = wave[sl(id, e)];
+              else v = load(pu, pv);
+              op(pu, pv, v);
+              return v;
+            },
+            [&](int id, int m, float2 v) {
+              const int k1 = id / ROWS;
+              wave[sl(id, m)] = m ? cmulc(v, twC[m * R1 + k1]) : v;
+            });
+      }
+    }
+  }
+
+  __device__ static void inverse_tail(float2* wave, const float2* twS, const float2* twC, int rank) {
+    col_strided<+1>(wave, twS, rank);
+    row_contig<+1>(wave, twC, rank);
+  }
+  __device__ static void forward_mid(float2* wave, const float2* twS, const float2* twC, int rank) {
+    row_contig<-1>(wave, twC, rank);
+    col_strided<-1>(wave, twS, rank);
+  }
+};
+
+}  // namespace ptycho
