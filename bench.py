@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--iterations", type=int, default=2, help="iterations per served request")
     ap.add_argument("--max-scan", type=int, default=48, help="largest scan side of a served request")
     ap.add_argument("--rate", type=float, default=16.0, help="mean request arrivals per second")
+    ap.add_argument("--precision", action="store_true",
+                    help="relative L2 error of every DFT mode against the FP64 oracle on a 4-position sub-problem")
     ap.add_argument("--group", type=int, default=0,
                     help="override the group size (small cases for profiling; not a bench line)")
     return ap.parse_args()
@@ -314,10 +316,53 @@ def run_serve(args):
     return 0
 
 
+def run_precision(args):
+    """Errors of intensities, loss and gradients against the FP64 oracle for
+    each DFT evaluation mode, on four neighbouring scan positions of the
+    workload (all slices and modes, full window; object cropped around them)."""
+    import torch
+    import oracle as orc
+    from paper_2505_14372_b300 import Context, synth
+    torch.cuda.set_device(0)
+    wl = synth.WORKLOADS[args.workload]
+    ny = wl.scan[1]
+    P = synth.probe_modes(wl)
+    pos = synth.raster_positions(wl)[[0, 1, ny, ny + 1]].astype(np.float64)
+    org = np.floor(pos.min(0)).astype(int) - 1
+    pos = (pos - org).astype(np.float32)
+    import dataclasses
+    small = dataclasses.replace(wl, H=wl.N + 8, W=wl.N + 8, atoms_per_slice=max(4, wl.atoms_per_slice // 20))
+    O = synth.phase_object(small)
+    E = synth.cbed_like_patterns(wl, 4)
+    og = orc.Geom(S=wl.S, K=wl.K, h=wl.N, w=wl.N, H=small.H, W=small.W, dx=wl.dx, lam=wl.lam, dz=wl.dz,
+                  bandlimit=wl.bandlimit, loss=wl.loss, eps=wl.eps, c=wl.c)
+    rI = orc.forward(O, P, pos, og)
+    L, rO, rP = orc.gradient(O, P, pos, E, og)
+    rel = lambda a, b: float(np.linalg.norm((np.asarray(a, np.complex128) - b).ravel()) / np.linalg.norm(b.ravel()))
+    out = {}
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    for mode in (["fft", "tf32x3", "bf16x3", "tf32"] if wl.N == 192 else ["fft"]):
+        geom = workload_geometry(small, args.waves, mode)
+        ctx = Context(geom, max_batch=4)
+        I = ctx.forward(d(O), d(P), d(pos)).cpu().numpy()
+        loss, gO, gP = ctx.adjoint(d(O), d(P), d(pos), d(E))
+        ctx.check_status()
+        out[mode] = {"I": rel(I, rI), "loss": abs(float(loss.item()) - L) / abs(L),
+                     "gO": rel(gO.cpu().numpy(), rO), "gP": rel(gP.cpu().numpy(), rP)}
+        ctx.close()
+    print(json.dumps({"mode": "precision", "metric": "relative L2 error against the FP64 oracle",
+                      "config": {"workload": wl.name, "positions": "4 neighbouring raster positions",
+                                 "object": [small.H, small.W], "waves": args.waves},
+                      "errors": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.serve:
         return run_serve(args)
+    if args.precision:
+        return run_precision(args)
     from paper_2505_14372_b300 import synth
     wl = synth.WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -24,6 +24,9 @@ namespace ptycho {
 
 enum TcMode { TC_NONE = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_TF32X1 = 3 };
 
+// words per lane in a fragment table (the TF32x3 size; BF16x3 uses half)
+constexpr int kTcLaneWords = 64;
+
 // registers of A fragments per lane for one (R, DIR) matrix
 template <int MODE>
 struct TcRegs {
@@ -67,7 +70,7 @@ struct TcMat {
   __device__ __forceinline__ void load(const uint32_t* table) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int i = 0; i < TcRegs<MODE>::N; ++i) a[i] = __ldg(table + lane * TcRegs<MODE>::N + i);
+    for (int i = 0; i < TcRegs<MODE>::N; ++i) a[i] = __ldg(table + lane * kTcLaneWords + i);
   }
 };
 

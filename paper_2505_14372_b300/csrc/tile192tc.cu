@@ -53,7 +53,7 @@ double dft_real(int R, int dir, int row, int col) {
 void fill_table(int mode, int R, int dir, uint32_t* out) {
   for (int lane = 0; lane < 32; ++lane) {
     const int g = lane / 4, t = lane % 4;
-    uint32_t* o = out + lane * 64;
+    uint32_t* o = out + lane * kTcLaneWords;
     if (mode == TC_BF16X3) {
       // m16n8k16 A fragment: {A[g][2t], A[g][2t+1]}, {A[g+8][..]}, {A[g][2t+8], ..}, {A[g+8][2t+8], ..}
       for (int mt = 0; mt < 2; ++mt)
