@@ -127,6 +127,16 @@ int ptycho_adjoint(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, co
                    int32_t B, const float* I_exp, double* loss_out, ptycho_c64* gO, ptycho_c64* gP,
                    int32_t accumulate, ptycho_stream stream);
 
+/* ptycho_adjoint plus the gradient with respect to the scan positions
+ * (position correction, §1 and §3: positions X_j are reconstruction
+ * variables): gpos_out[B][2] (device double, d L / d(y, x) in object pixels)
+ * is overwritten, or added to when accumulate != 0.  The derivative goes
+ * through the sub-pixel Fourier ramp; the integer patch origin is piecewise
+ * constant. */
+int ptycho_adjoint_positions(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
+                             int32_t B, const float* I_exp, double* loss_out, ptycho_c64* gO, ptycho_c64* gP,
+                             double* gpos_out, int32_t accumulate, ptycho_stream stream);
+
 /* Vector-Jacobian product of the forward model (§3.2: the gradient engine
  * of the paper is the VJP of the forward simulation): for a cotangent
  * gI[B][N][N] = dL/dI of any real loss L(I), writes (or adds, accumulate

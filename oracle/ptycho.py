@@ -48,6 +48,14 @@ listed in DESIGN.md):
   R8  Complex Adam: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2)|g|^2 (real),
       z <- z - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps_adam).
   R9  Incoherent mode weights are carried by the mode amplitudes.
+  R10 Gaussian noise model (§3.1): l = (I - I_exp)^2 / (2 sigma^2), the
+      normalisation constant dropped; sigma is passed in the c field.
+  R11 Cost regularisers (§3.4) act on the complex transmission and the probe
+      (the paper names the phase; for weak phase objects |grad O|^2 is
+      |grad phase|^2): object L2 lambda sum |O - 1|^2 (vacuum is O = 1),
+      probe L2 lambda sum |P|^2, in-plane Tikhonov lambda sum of squared
+      forward differences along y and x inside each slice, and Tikhonov
+      across layers lambda sum_s |O_{s+1} - O_s|^2.
 """
 from __future__ import annotations
 
@@ -59,13 +67,14 @@ import numpy as np
 
 AMPLITUDE = 0
 POISSON = 1
+GAUSSIAN = 2
 
 __all__ = [
     "AMPLITUDE", "POISSON", "Geom", "freq_index", "dft_matrix", "dft2",
     "idft2", "dft2_ortho", "idft2_ortho", "split_positions", "shift_ramp",
     "shift_probe", "bandlimit_mask", "propagator", "propagate",
     "forward", "forward_waves", "loss_terms", "loss_value", "gradient",
-    "adam_update", "step", "position_gradient", "vjp",
+    "adam_update", "step", "position_gradient", "vjp", "GAUSSIAN", "regularizers",
 ]
 
 
@@ -251,6 +260,9 @@ def loss_terms(I, I_exp, g: Geom):
     if g.loss == POISSON:
         l = I - E - E * (np.log(I + g.eps) - np.log(E + g.eps))
         return l, 1.0 - E / (I + g.eps)
+    if g.loss == GAUSSIAN:
+        s2 = g.c * g.c
+        return (I - E) ** 2 / (2.0 * s2), (I - E) / s2
     raise ValueError("unknown loss")
 
 
@@ -338,6 +350,37 @@ def position_gradient(O, P, pos, I_exp, g: Geom) -> np.ndarray:
     return out
 
 
+# ---------------------------------------------------- regularisers (§3.4)
+
+def regularizers(O, P, l2_obj=0.0, tikhonov=0.0, layers=0.0, l2_probe=0.0):
+    """Cost-regulariser value and gradients (R7 convention) (R11)."""
+    O = np.asarray(O, dtype=np.complex128)
+    P = np.asarray(P, dtype=np.complex128)
+    val = 0.0
+    gO = np.zeros_like(O)
+    gP = np.zeros_like(P)
+    if l2_obj:
+        val += l2_obj * float(np.sum(np.abs(O - 1.0) ** 2))
+        gO += 2.0 * l2_obj * (O - 1.0)
+    if l2_probe:
+        val += l2_probe * float(np.sum(np.abs(P) ** 2))
+        gP += 2.0 * l2_probe * P
+    if tikhonov:
+        dy = O[:, 1:, :] - O[:, :-1, :]
+        dx = O[:, :, 1:] - O[:, :, :-1]
+        val += tikhonov * float(np.sum(np.abs(dy) ** 2) + np.sum(np.abs(dx) ** 2))
+        gO[:, 1:, :] += 2.0 * tikhonov * dy
+        gO[:, :-1, :] -= 2.0 * tikhonov * dy
+        gO[:, :, 1:] += 2.0 * tikhonov * dx
+        gO[:, :, :-1] -= 2.0 * tikhonov * dx
+    if layers and O.shape[0] > 1:
+        dz = O[1:] - O[:-1]
+        val += layers * float(np.sum(np.abs(dz) ** 2))
+        gO[1:] += 2.0 * layers * dz
+        gO[:-1] -= 2.0 * layers * dz
+    return val, gO, gP
+
+
 # ----------------------------------------------------------- Adam (§3.2)
 
 def adam_update(z, m, v, gz, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):
@@ -351,15 +394,19 @@ def adam_update(z, m, v, gz, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def step(O, P, mO, vO, mP, vP, t, pos_all, I_exp_all, idx, g: Geom,
-         lr_O, lr_P, b1=0.9, b2=0.999, eps_adam=1e-8, update_probe=True):
+         lr_O, lr_P, b1=0.9, b2=0.999, eps_adam=1e-8, update_probe=True, reg=None):
     """One gradient-descent iteration on the minibatch idx (§2.2 grouping,
-    §3.2 solver).  t is the Adam step count AFTER this step.  Returns
+    §3.2 solver, optional §3.4 cost regularisers `reg`, a dict of
+    regularizers() weights).  t is the Adam step count AFTER this step.  Returns
     (O, P, mO, vO, mP, vP, loss, gnorm) where gnorm = sqrt(sum |g|^2) over
     the object and probe gradients."""
     idx = np.asarray(idx, dtype=np.int64)
     pos = np.asarray(pos_all, dtype=np.float64).reshape(-1, 2)[idx]
     E = np.asarray(I_exp_all, dtype=np.float64).reshape(-1, g.h, g.w)[idx]
     loss, gO, gP = gradient(O, P, pos, E, g)
+    if reg:
+        rv, rO, rP = regularizers(O, P, **reg)
+        loss, gO, gP = loss + rv, gO + rO, gP + rP
     gnorm = math.sqrt(float(np.sum(np.abs(gO) ** 2) + np.sum(np.abs(gP) ** 2)))
     O2, mO, vO = adam_update(np.asarray(O, np.complex128), mO, vO, gO, t, lr_O, b1, b2, eps_adam)
     if update_probe:

@@ -73,6 +73,7 @@ SIGNATURES = {
     "ptycho_forward": (I32, [P_, P_, P_, P_, I32, P_, P_]),
     "ptycho_adjoint": (I32, [P_, P_, P_, P_, I32, P_, P_, P_, P_, I32, P_]),
     "ptycho_vjp": (I32, [P_, P_, P_, P_, I32, P_, P_, P_, I32, P_]),
+    "ptycho_adjoint_positions": (I32, [P_, P_, P_, P_, I32, P_, P_, P_, P_, P_, I32, P_]),
     "ptycho_forward_static": (I32, [C.POINTER(Geom), P_, P_, P_, I32, P_, P_]),
     "ptycho_step": (I32, [P_, P_, P_, C.POINTER(Adam), C.POINTER(Opt), P_, P_, I32, P_, I32, P_, P_]),
     "ptycho_step_host": (I32, [P_, P_, P_, C.POINTER(Adam), C.POINTER(Opt), P_, P_, I32,

@@ -138,6 +138,22 @@ class Context:
                                    _ptr(gO), _ptr(gP), 1 if accumulate else 0, _stream()))
         return loss, gO, gP
 
+    def adjoint_positions(self, O, P, pos, I_exp, gO=None, gP=None, gpos=None, accumulate=False):
+        """Returns (loss, gO, gP, gpos [B, 2] float64 device tensor)."""
+        B = pos.shape[0]
+        g = self.geom
+        _need(O, torch.complex64, self._oshape(), "O")
+        _need(P, torch.complex64, self._pshape(), "P")
+        _need(pos, torch.float32, (B, 2), "pos")
+        _need(I_exp, torch.float32, (B, g.N, g.N), "I_exp")
+        gO = torch.empty_like(O) if gO is None else gO
+        gP = torch.empty_like(P) if gP is None else gP
+        gpos = torch.empty((B, 2), dtype=torch.float64, device=O.device) if gpos is None else gpos
+        loss = torch.zeros((), dtype=torch.float64, device=O.device)
+        check(lib().ptycho_adjoint_positions(self.h, _ptr(O), _ptr(P), _ptr(pos), B, _ptr(I_exp), _ptr(loss),
+                                             _ptr(gO), _ptr(gP), _ptr(gpos), 1 if accumulate else 0, _stream()))
+        return loss, gO, gP, gpos
+
     def vjp(self, O, P, pos, gI, gO=None, gP=None, accumulate=False):
         B = pos.shape[0]
         g = self.geom

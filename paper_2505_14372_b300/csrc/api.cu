@@ -218,7 +218,7 @@ int check_call(ptycho_ctx* c, int B) {
 // noise model's derivative (vector-Jacobian product).
 int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, const int* idx, int B,
                  int npos, const float* Iexp, ptycho_c64* gO, ptycho_c64* gP, int accumulate, cudaStream_t s, int* nl_out,
-                 bool vjp = false, const float* gI = nullptr) {
+                 bool vjp = false, const float* gI = nullptr, double* gpos = nullptr) {
   const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
   const int K = c->g.K;
   float2* Phat = reinterpret_cast<float2*>(c->arena + L.Phat);
@@ -240,6 +240,8 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   }
   ProblemDesc d = base_desc(c, L, O, pos, idx, B, npos);
   d.gO = reinterpret_cast<float2*>(gO);
+  d.gpos = gpos;
+  if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
   LaunchArgs la = one_problem(c, L, d);
   const int items = B * K;
   {
@@ -419,6 +421,24 @@ int ptycho_adjoint(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, cons
   if (loss_out) {
     const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
     Timed t(c, "finalize", s);
+    CK(ptycho::launch_finalize(reinterpret_cast<double*>(c->arena + L.partials), nl, 0, loss_out, 0, s));
+  }
+  return PTYCHO_OK;
+}
+
+int ptycho_adjoint_positions(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
+                             const float* I_exp, double* loss_out, ptycho_c64* gO, ptycho_c64* gP, double* gpos_out,
+                             int32_t accumulate, ptycho_stream stream) {
+  int rc = check_call(c, B);
+  if (rc) return rc;
+  if (!O || !P || (B > 0 && (!pos || !I_exp || !gpos_out)) || !gO || !gP)
+    return perr(PTYCHO_EINVAL, "NULL array argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int nl = 0;
+  rc = run_gradient(c, O, P, pos, nullptr, B, B, I_exp, gO, gP, accumulate, s, &nl, false, nullptr, gpos_out);
+  if (rc) return rc;
+  if (loss_out) {
+    const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
     CK(ptycho::launch_finalize(reinterpret_cast<double*>(c->arena + L.partials), nl, 0, loss_out, 0, s));
   }
   return PTYCHO_OK;

@@ -202,13 +202,38 @@ __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
       __syncthreads();
       TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
     } else {
-      // F g_psi_0 -> conj(ramp) -> accumulate the probe spectrum gradient
+      // F g_psi_0 -> conj(ramp) -> accumulate the probe spectrum gradient.
+      // Position gradient (through the ramp only; the patch origin is
+      // piecewise constant): dL/d(delta_y) = 2 pi / (N NP) sum f_u Im(w),
+      // w = conj(F g_psi_0) ramp F P, likewise for x with f_v.
       float2* gP = D.gPhat + (size_t)g.k * TL::NP;
+      const float2* Ph = D.Phat + (size_t)g.k * TL::NP;
       const float2* rY = sm.rampY;
       const float2* rX = sm.rampX;
+      const bool want_pos = D.gpos != nullptr;
+      float sy = 0.f, sx = 0.f;
       TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
-        red_add(gP + pu * N + pv, cmulc(v, cmul(rY[pu], rX[pv])));
+        const float2 ramp = cmul(rY[pu], rX[pv]);
+        red_add(gP + pu * N + pv, cmulc(v, ramp));
+        if (want_pos) {
+          const float w = cconjmul(v, cmul(ramp, __ldg(Ph + pu * N + pv))).y;
+          sy = fmaf((float)TL::freq(TL::nat(pu)), w, sy);
+          sx = fmaf((float)TL::freq(TL::nat(pv)), w, sx);
+        }
       });
+      if (want_pos) {
+        double dy = sy, dx = sx;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          dy += __shfl_xor_sync(0xffffffffu, dy, o);
+          dx += __shfl_xor_sync(0xffffffffu, dx, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+          const double sc = 2.0 * 3.14159265358979323846 / ((double)N * (double)TL::NP);
+          atomicAdd(D.gpos + 2 * (size_t)g.j, sc * dy);
+          atomicAdd(D.gpos + 2 * (size_t)g.j + 1, sc * dx);
+        }
+      }
     }
   }
 }

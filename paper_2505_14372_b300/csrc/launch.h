@@ -20,6 +20,7 @@ struct ProblemDesc {
   float2* waves;        // STORE: [B][K][S][NP] entry waves (natural order)
   float2* gO;           // [S][H][W] object gradient (accumulated)
   float2* gPhat;        // [K][NP] probe spectrum gradient (accumulated)
+  double* gpos;         // [B][2] scan-position gradient (accumulated), or null
   int S, K, H, W, B;
   int npos;             // rows of pos (and of the pattern array) idx may select
   int blT;              // band limit keeps f_u^2 + f_v^2 <= blT; < 0: off

@@ -145,3 +145,16 @@ def test_invalid_arguments():
     ctx = Context(geom, max_batch=2)
     with pytest.raises(PtychoError):
         ctx.forward(dev(O), dev(P), dev(pos))   # B = 3 > max_batch
+
+
+@pytest.mark.parametrize("N,S,K,H,W", [(64, 2, 2, 80, 84), (192, 2, 2, 200, 200)])
+def test_position_gradient_parity(N, S, K, H, W):
+    geom, og, P, O, pos = problem(61 + N, S, K, N, H, W, 5, loss="poisson", eps=0.8)
+    I_exp = np.random.default_rng(8).poisson(orc.forward(O, P, pos, og) * 1.2 + 0.3).astype(np.float32)
+    ctx = Context(geom, max_batch=5)
+    loss, gO, gP, gpos = ctx.adjoint_positions(dev(O), dev(P), dev(pos), dev(I_exp))
+    ref = orc.position_gradient(O, P, pos, I_exp, og)
+    assert rel_l2(host(gpos), ref) < TOL_MS
+    # the other outputs are those of ptycho_adjoint
+    L, rO, rP = orc.gradient(O, P, pos, I_exp, og)
+    assert rel_l2(host(gO), rO) < TOL_MS and rel_l2(host(gP), rP) < TOL_MS

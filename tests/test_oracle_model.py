@@ -359,3 +359,43 @@ def test_vjp_is_gradient_of_linearised_loss():
     d = crand(2, 8, 8)
     fd = (np.sum(cI * orc.forward(O, P + h * d, POS4, g)) - np.sum(cI * orc.forward(O, P - h * d, POS4, g))) / (2 * h)
     assert abs(fd - np.real(np.vdot(gP, d))) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_gaussian_model_and_fd():
+    g = tiny(loss=orc.GAUSSIAN, c=3.0, eps=0.0)
+    I = RNG.random((6, 6)) * 40
+    E = RNG.poisson(I).astype(float)
+    l, dl = orc.loss_terms(I, E, g)
+    # negative log-likelihood of N(I, sigma^2) up to its constant
+    nll = -np.log(np.exp(-(I - E) ** 2 / (2 * 9.0)) / (3.0 * np.sqrt(2 * np.pi)))
+    assert np.allclose(nll - l, np.log(3.0 * np.sqrt(2 * np.pi)))
+    h = 1e-6
+    assert np.allclose((orc.loss_terms(I + h, E, g)[0] - orc.loss_terms(I - h, E, g)[0]) / (2 * h), dl, rtol=1e-6,
+                       atol=1e-9)
+
+
+@pytest.mark.parametrize("kw", [dict(l2_obj=0.3), dict(l2_probe=0.2), dict(tikhonov=0.4), dict(layers=0.5),
+                                dict(l2_obj=0.1, tikhonov=0.2, layers=0.3, l2_probe=0.05)])
+def test_regularizer_gradients_by_fd(kw):
+    O = crand(3, 5, 6)
+    P = crand(2, 4, 4)
+    val, gO, gP = orc.regularizers(O, P, **kw)
+    h = 1e-6
+    for arr, grad, which in ((O, gO, "O"), (P, gP, "P")):
+        for ix in list(np.ndindex(arr.shape))[::7]:
+            for unit in (1.0, 1j):
+                a1, a2 = arr.copy(), arr.copy()
+                a1[ix] += h * unit
+                a2[ix] -= h * unit
+                args1 = (a1, P) if which == "O" else (O, a1)
+                args2 = (a2, P) if which == "O" else (O, a2)
+                fd = (orc.regularizers(*args1, **kw)[0] - orc.regularizers(*args2, **kw)[0]) / (2 * h)
+                an = grad[ix].real if unit == 1.0 else grad[ix].imag
+                assert abs(fd - an) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_regularizers_vanish_on_their_null_space():
+    O = np.ones((3, 5, 5), complex) * np.exp(0.3j)    # constant in plane and depth
+    P = crand(1, 4, 4)
+    assert orc.regularizers(O, P, tikhonov=1.0, layers=1.0)[0] < 1e-24
+    assert orc.regularizers(np.ones((2, 3, 3), complex), P, l2_obj=1.0)[0] == 0.0
