@@ -68,7 +68,8 @@ typedef struct {
 /* cudaStream_t; NULL is the legacy default stream. */
 typedef void* ptycho_stream;
 
-typedef enum { PTYCHO_LOSS_AMPLITUDE = 0, PTYCHO_LOSS_POISSON = 1 } ptycho_loss;
+/* Noise models (§3.1); GAUSSIAN: (I - I_exp)^2 / (2 c^2), c = sigma > 0. */
+typedef enum { PTYCHO_LOSS_AMPLITUDE = 0, PTYCHO_LOSS_POISSON = 1, PTYCHO_LOSS_GAUSSIAN = 2 } ptycho_loss;
 
 /* How the adjoint gets the entry wave of every slice: STORE keeps all of
  * them from the forward pass (B*K*S*N*N*8 bytes of scratch), RECOMPUTE
@@ -166,11 +167,16 @@ int ptycho_vjp(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, const 
 int ptycho_forward_static(const ptycho_geom* geom, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
                           int32_t B, float* I_out, ptycho_stream stream);
 
-/* Adam hyper-parameters (§3.2; Optax-style defaults 0.9, 0.999, 1e-8). */
+/* Adam hyper-parameters (§3.2; Optax-style defaults 0.9, 0.999, 1e-8) and
+ * the weights of the cost regularisers added to the loss (§3.4; 0 = off):
+ * object L2 lambda sum |O - 1|^2, in-plane Tikhonov lambda sum of squared
+ * forward differences along y and x of every slice, Tikhonov across layers
+ * lambda sum |O_{s+1} - O_s|^2, probe L2 lambda sum |P|^2. */
 typedef struct {
   float lr_O, lr_P;
   float beta1, beta2, eps;
   int32_t update_probe; /* 0: the probe is held fixed */
+  float reg_obj_l2, reg_obj_tikhonov, reg_obj_layers, reg_probe_l2;
 } ptycho_opt;
 
 /* Adam state: first moments m (complex64), second moments v (float32, |g|^2

@@ -32,7 +32,8 @@ class Geom(C.Structure):
 
 class Opt(C.Structure):
     _fields_ = [("lr_O", C.c_float), ("lr_P", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float), ("update_probe", C.c_int32)]
+                ("eps", C.c_float), ("update_probe", C.c_int32), ("reg_obj_l2", C.c_float),
+                ("reg_obj_tikhonov", C.c_float), ("reg_obj_layers", C.c_float), ("reg_probe_l2", C.c_float)]
 
 
 class Adam(C.Structure):

@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import check, lib
 
-LOSS = {"amplitude": 0, "anscombe": 0, "poisson": 1}
+LOSS = {"amplitude": 0, "anscombe": 0, "poisson": 1, "gaussian": 2}
 WAVES = {"auto": 0, "store": 1, "recompute": 2}
 DFT = {"fft": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3}
 
@@ -60,8 +60,10 @@ class Geometry:
         return g, dz
 
 
-def adam_opt(lr_O=1e-3, lr_P=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, update_probe=True) -> _lib.Opt:
-    return _lib.Opt(lr_O, lr_P, beta1, beta2, eps, 1 if update_probe else 0)
+def adam_opt(lr_O=1e-3, lr_P=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, update_probe=True, reg_obj_l2=0.0,
+             reg_obj_tikhonov=0.0, reg_obj_layers=0.0, reg_probe_l2=0.0) -> _lib.Opt:
+    return _lib.Opt(lr_O, lr_P, beta1, beta2, eps, 1 if update_probe else 0, reg_obj_l2, reg_obj_tikhonov,
+                    reg_obj_layers, reg_probe_l2)
 
 
 class AdamState:

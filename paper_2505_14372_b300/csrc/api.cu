@@ -40,7 +40,7 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   L.A = take((size_t)B * g.K * NP * 8);
   L.w = take((size_t)B * NP * 4);
   L.gPhat = take((size_t)g.K * NP * 8);
-  L.partials = take((size_t)(ptycho::kLossBlocks + 2 * ptycho::kNormBlocks + 8) * 8);
+  L.partials = take((size_t)(ptycho::kLossBlocks + 3 * ptycho::kNormBlocks + 8) * 8);
   L.stats = take(4 * 8);
   L.stage_pos = take((size_t)B * 2 * 4);
   L.stage_I = take((size_t)B * NP * 4);
@@ -65,8 +65,9 @@ int validate_geom(const ptycho_geom* g) {
   for (int i = 0; i + 1 < g->S; ++i)
     if (!std::isfinite(g->dz[i])) return perr(PTYCHO_EINVAL, "dz must be finite");
   if (!std::isfinite(g->bandlimit)) return perr(PTYCHO_EINVAL, "bandlimit must be finite");
-  if (g->loss != PTYCHO_LOSS_AMPLITUDE && g->loss != PTYCHO_LOSS_POISSON)
+  if (g->loss != PTYCHO_LOSS_AMPLITUDE && g->loss != PTYCHO_LOSS_POISSON && g->loss != PTYCHO_LOSS_GAUSSIAN)
     return perr(PTYCHO_EINVAL, "unknown loss");
+  if (g->loss == PTYCHO_LOSS_GAUSSIAN && !(g->c > 0)) return perr(PTYCHO_EINVAL, "Gaussian loss needs sigma = c > 0");
   if (!(g->eps >= 0) || !(g->c >= 0)) return perr(PTYCHO_EINVAL, "eps and c must be >= 0");
   if (g->loss == PTYCHO_LOSS_POISSON && !(g->eps > 0)) return perr(PTYCHO_EINVAL, "Poisson loss needs eps > 0");
   if (g->loss == PTYCHO_LOSS_AMPLITUDE && !(g->eps + g->c > 0))
@@ -472,11 +473,20 @@ static int step_impl(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
   double* stats = stats_out ? stats_out : reinterpret_cast<double*>(c->arena + L.stats);
   const long long nO = (long long)c->g.S * c->g.H * c->g.W;
   const long long nP = (long long)c->g.K * c->NP;
+  const bool reg = opt->reg_obj_l2 != 0.f || opt->reg_obj_tikhonov != 0.f || opt->reg_obj_layers != 0.f ||
+                   opt->reg_probe_l2 != 0.f;
+  const int nr = reg ? ptycho::kNormBlocks : 0;
+  if (reg) {
+    Timed t(c, "regularize", s);
+    CK(ptycho::launch_regularize(reinterpret_cast<const float2*>(O), c->gO, c->g.S, c->g.H, c->g.W,
+                                 reinterpret_cast<const float2*>(P), c->gP, nP, opt->reg_obj_l2,
+                                 opt->reg_obj_tikhonov, opt->reg_obj_layers, opt->reg_probe_l2, partials + nl, nr, s));
+  }
   {
     Timed t(c, "reduce", s);
-    CK(ptycho::launch_sumsq(c->gO, nO, partials + nl, ptycho::kNormBlocks, s));
-    CK(ptycho::launch_sumsq(c->gP, nP, partials + nl + ptycho::kNormBlocks, ptycho::kNormBlocks, s));
-    CK(ptycho::launch_finalize(partials, nl, 2 * ptycho::kNormBlocks, stats, 1, s));
+    CK(ptycho::launch_sumsq(c->gO, nO, partials + nl + nr, ptycho::kNormBlocks, s));
+    CK(ptycho::launch_sumsq(c->gP, nP, partials + nl + nr + ptycho::kNormBlocks, ptycho::kNormBlocks, s));
+    CK(ptycho::launch_finalize(partials, nl + nr, 2 * ptycho::kNormBlocks, stats, 1, s));
   }
   const int64_t t = st->t + 1;
   const float bc1 = (float)(1.0 / (1.0 - std::pow((double)opt->beta1, (double)t)));
@@ -659,9 +669,15 @@ int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long 
     double* partials = reinterpret_cast<double*>(c->arena + L[i].partials);
     const long long nO = (long long)c->g.S * c->g.H * c->g.W, nP = (long long)c->g.K * c->NP;
     CK(ops->probe_grad(reinterpret_cast<float2*>(c->arena + L[i].gPhat), c->gP, c->g.K, 0, s));
-    CK(launch_sumsq(c->gO, nO, partials + nl[i], kNormBlocks, s));
-    CK(launch_sumsq(c->gP, nP, partials + nl[i] + kNormBlocks, kNormBlocks, s));
-    CK(launch_finalize(partials, nl[i], 2 * kNormBlocks, J.stats, 1, s));
+    const bool reg = J.opt.reg_obj_l2 != 0.f || J.opt.reg_obj_tikhonov != 0.f || J.opt.reg_obj_layers != 0.f ||
+                     J.opt.reg_probe_l2 != 0.f;
+    const int nr = reg ? kNormBlocks : 0;
+    if (reg)
+      CK(launch_regularize(J.O, c->gO, c->g.S, c->g.H, c->g.W, J.P, c->gP, nP, J.opt.reg_obj_l2,
+                           J.opt.reg_obj_tikhonov, J.opt.reg_obj_layers, J.opt.reg_probe_l2, partials + nl[i], nr, s));
+    CK(launch_sumsq(c->gO, nO, partials + nl[i] + nr, kNormBlocks, s));
+    CK(launch_sumsq(c->gP, nP, partials + nl[i] + nr + kNormBlocks, kNormBlocks, s));
+    CK(launch_finalize(partials, nl[i] + nr, 2 * kNormBlocks, J.stats, 1, s));
     const double t = (double)J.t;
     const float bc1 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta1, t)));
     const float bc2 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta2, t)));

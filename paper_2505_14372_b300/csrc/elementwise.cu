@@ -66,6 +66,79 @@ __global__ void k_adam(float2* __restrict__ z, float2* __restrict__ m, float* __
 }
 
 
+// Cost regularisers (arXiv 2505.14372 §3.4) on the complex transmission and
+// the probe: adds their gradients (dL/dRe z + i dL/dIm z) to gO / gP and
+// writes block partial sums of their value.  Object elements [0, nO), probe
+// elements [nO, nO + nP).  Object L2 penalises the distance to vacuum
+// (O = 1); Tikhonov terms use forward differences inside each slice (y, x)
+// and across layers (s).
+__global__ void __launch_bounds__(kRedThreads) k_regularize(const float2* __restrict__ O, float2* __restrict__ gO,
+                                                            int S, int H, int W, const float2* __restrict__ P,
+                                                            float2* __restrict__ gP, long long nP, float l2,
+                                                            float tik, float lay, float l2p,
+                                                            double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const long long HW = (long long)H * W, nO = (long long)S * HW;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nO + nP;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e >= nO) {
+      const long long i = e - nO;
+      const float2 p = P[i];
+      acc += (double)l2p * cabs2(p);
+      float2 g = gP[i];
+      g.x += 2.f * l2p * p.x;
+      g.y += 2.f * l2p * p.y;
+      gP[i] = g;
+      continue;
+    }
+    const int s = (int)(e / HW);
+    const long long r = e - (long long)s * HW;
+    const int y = (int)(r / W), x = (int)(r - (long long)y * W);
+    const float2 o = O[e];
+    float gx = 0.f, gy = 0.f;
+    float val = 0.f;
+    if (l2 != 0.f) {
+      const float dx_ = o.x - 1.f, dy_ = o.y;
+      val += l2 * (dx_ * dx_ + dy_ * dy_);
+      gx += 2.f * l2 * dx_;
+      gy += 2.f * l2 * dy_;
+    }
+    auto edge = [&](float lam, long long nb, bool fwd) {
+      const float2 q = O[nb];
+      const float dx_ = o.x - q.x, dy_ = o.y - q.y;
+      if (fwd) val += lam * (dx_ * dx_ + dy_ * dy_);  // each difference counted once
+      gx += 2.f * lam * dx_;
+      gy += 2.f * lam * dy_;
+    };
+    if (tik != 0.f) {
+      if (y + 1 < H) edge(tik, e + W, true);
+      if (y > 0) edge(tik, e - W, false);
+      if (x + 1 < W) edge(tik, e + 1, true);
+      if (x > 0) edge(tik, e - 1, false);
+    }
+    if (lay != 0.f) {
+      if (s + 1 < S) edge(lay, e + HW, true);
+      if (s > 0) edge(lay, e - HW, false);
+    }
+    float2 g = gO[e];
+    g.x += gx;
+    g.y += gy;
+    gO[e] = g;
+    acc += (double)val;
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+cudaError_t launch_regularize(const float2* O, float2* gO, int S, int H, int W, const float2* P, float2* gP,
+                              long long nP, float l2, float tik, float lay, float l2p, double* partials, int nblocks,
+                              cudaStream_t s) {
+  count_launch();
+  k_regularize<<<nblocks, kRedThreads, 0, s>>>(O, gO, S, H, W, P, gP, nP, l2, tik, lay, l2p, partials);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sumsq(const float2* g, long long n, double* partials, int nblocks, cudaStream_t s) {
   count_launch();
   k_sumsq<<<nblocks, kRedThreads, 0, s>>>(g, n, partials);

@@ -45,6 +45,9 @@ inline const EngineOps* engine_for(int N, int dft = 0) {
 cudaError_t launch_sumsq(const float2* g, long long n, double* partials, int nblocks, cudaStream_t s);
 cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out, int sqrt_second,
                             cudaStream_t s);
+cudaError_t launch_regularize(const float2* O, float2* gO, int S, int H, int W, const float2* P, float2* gP,
+                              long long nP, float l2, float tik, float lay, float l2p, double* partials, int nblocks,
+                              cudaStream_t s);
 cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long long n, float lr, float b1,
                         float b2, float eps, float bc1, float bc2, cudaStream_t s);
 

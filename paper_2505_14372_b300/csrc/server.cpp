@@ -481,7 +481,9 @@ int ptycho_submit(ptycho_server* s, const ptycho_request* q, uint64_t* ticket) {
     if (!(g.dx > 0) || !(g.lambda > 0)) return perr(PTYCHO_EINVAL, "dx and lambda must be > 0");
     if (g.loss == PTYCHO_LOSS_POISSON && !(g.eps > 0)) return perr(PTYCHO_EINVAL, "Poisson loss needs eps > 0");
     if (g.loss == PTYCHO_LOSS_AMPLITUDE && !(g.eps + g.c > 0)) return perr(PTYCHO_EINVAL, "amplitude needs eps + c > 0");
-    if (g.loss != PTYCHO_LOSS_POISSON && g.loss != PTYCHO_LOSS_AMPLITUDE) return perr(PTYCHO_EINVAL, "unknown loss");
+    if (g.loss != PTYCHO_LOSS_POISSON && g.loss != PTYCHO_LOSS_AMPLITUDE && g.loss != PTYCHO_LOSS_GAUSSIAN)
+      return perr(PTYCHO_EINVAL, "unknown loss");
+    if (g.loss == PTYCHO_LOSS_GAUSSIAN && !(g.c > 0)) return perr(PTYCHO_EINVAL, "Gaussian loss needs c > 0");
   }
   for (int j = 0; j < q->n_pos; ++j) {
     const double y = std::floor((double)q->pos[2 * j] + 0.5), x = std::floor((double)q->pos[2 * j + 1] + 0.5);

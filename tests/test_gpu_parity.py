@@ -158,3 +158,33 @@ def test_position_gradient_parity(N, S, K, H, W):
     # the other outputs are those of ptycho_adjoint
     L, rO, rP = orc.gradient(O, P, pos, I_exp, og)
     assert rel_l2(host(gO), rO) < TOL_MS and rel_l2(host(gP), rP) < TOL_MS
+
+
+def test_gaussian_noise_model_parity():
+    geom, og, P, O, pos = problem(71, 2, 2, 64, 84, 80, 7, loss="amplitude")
+    geom.loss, geom.c, geom.eps = "gaussian", 4.0, 0.0
+    og.loss, og.c, og.eps = orc.GAUSSIAN, 4.0, 0.0
+    I_exp = np.random.default_rng(4).poisson(orc.forward(O, P, pos, og) * 1.1 + 0.5).astype(np.float32)
+    ctx = Context(geom, max_batch=7)
+    loss, gO, gP = ctx.adjoint(dev(O), dev(P), dev(pos), dev(I_exp))
+    L, rO, rP = orc.gradient(O, P, pos, I_exp, og)
+    assert abs(float(loss.item()) - L) < TOL_MS * abs(L)
+    assert rel_l2(host(gO), rO) < TOL_MS and rel_l2(host(gP), rP) < TOL_MS
+
+
+def test_step_with_regularizers_parity():
+    geom, og, P, O, pos = problem(73, 3, 2, 64, 90, 90, 10, loss="poisson", eps=0.8)
+    I_exp = np.random.default_rng(6).poisson(orc.forward(O, P, pos, og) + 0.5).astype(np.float32)
+    reg = dict(l2_obj=0.05, tikhonov=0.05, layers=0.5, l2_probe=1e-3)
+    idx = np.array([1, 4, 7, 9, 0], np.int32)
+    ctx = Context(geom, max_batch=5)
+    Od, Pd = dev(O), dev(P)
+    st = AdamState(geom)
+    opt = adam_opt(lr_O=1e-2, lr_P=1e-3, reg_obj_l2=reg["l2_obj"], reg_obj_tikhonov=reg["tikhonov"],
+                   reg_obj_layers=reg["layers"], reg_probe_l2=reg["l2_probe"])
+    stats = host(ctx.step(Od, Pd, st, opt, dev(pos), dev(I_exp), dev(idx)))
+    z = np.zeros
+    O2, P2, *_, L, gn = orc.step(O, P, z(O.shape, complex), z(O.shape), z(P.shape, complex), z(P.shape), 1, pos,
+                                 I_exp, idx, og, 1e-2, 1e-3, reg=reg)
+    assert abs(stats[0] - L) < TOL_MS * abs(L) and abs(stats[1] - gn) < TOL_MS * gn
+    assert rel_l2(host(Od), O2) < 1e-5 and rel_l2(host(Pd), P2) < 1e-5
