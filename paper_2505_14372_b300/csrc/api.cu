@@ -24,7 +24,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Offsets of one call's scratch inside the context arena.
 struct Layout {
-  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, waves, total;
+  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, cnt, waves, total;
 };
 
 Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
@@ -40,10 +40,13 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   L.A = take((size_t)B * g.K * NP * 8);
   L.w = take((size_t)B * NP * 4);
   L.gPhat = take((size_t)g.K * NP * 8);
-  L.partials = take((size_t)(ptycho::kLossBlocks + 3 * ptycho::kNormBlocks + 8) * 8);
+  // loss partials: block sums of the loss kernel, or one per position for
+  // the fused kernel; then regulariser and gradient-norm partials
+  L.partials = take((size_t)(std::max(ptycho::kLossBlocks, B) + 3 * ptycho::kNormBlocks + 8) * 8);
   L.stats = take(4 * 8);
   L.stage_pos = take((size_t)B * 2 * 4);
   L.stage_I = take((size_t)B * NP * 4);
+  L.cnt = take((size_t)B * 4);
   L.waves = take(store ? (size_t)B * g.K * g.S * NP * 8 : (size_t)slots * g.S * NP * 8);
   L.total = off;
   return L;
@@ -105,6 +108,7 @@ struct ptycho_ctx {
   size_t arena_bytes = 0;
   bool store = true;
   int slots = 0;          // recompute slots (clusters of the recompute adjoint)
+  int fused_clusters = 0; // resident clusters of the fused loss + adjoint kernel
   int res_fwd = 1, res_adj = 1;
   // timing
   bool timing = false;
@@ -242,7 +246,39 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   ProblemDesc d = base_desc(c, L, O, pos, idx, B, npos);
   d.gO = reinterpret_cast<float2*>(gO);
   d.gpos = gpos;
-  if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
+  // Entry waves recomputed: one fused loss + adjoint launch when all mode
+  // clusters of a round fit on the device at once (cooperative launch).
+  if (!c->store && !vjp && c->fused_clusters >= K) {
+    if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
+    ptycho::FusedArgs F{};
+    F.Iexp = Iexp;
+    F.Ibuf = reinterpret_cast<float*>(c->arena + L.A);
+    F.cnt = reinterpret_cast<unsigned*>(c->arena + L.cnt);
+    F.lpart = partials;
+    F.model = c->g.loss;
+    F.eps = (float)c->g.eps;
+    F.c = (float)c->g.c;
+    F.groups = c->fused_clusters / K;
+    CK(cudaMemsetAsync(F.cnt, 0, (size_t)B * 4, s));
+    CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
+    LaunchArgs la = one_problem(c, L, d);
+    cudaError_t e;
+    {
+      Timed t(c, "adjoint", s);
+      e = c->ops->adjoint_fused(la, F, F.groups * K, s);
+    }
+    if (e == cudaSuccess) {
+      *nl_out = B;
+      Timed t(c, "probe_grad", s);
+      CK(c->ops->probe_grad(gPhat, reinterpret_cast<float2*>(gP), K, accumulate, s));
+      return PTYCHO_OK;
+    }
+    // the device refused the cooperative launch: take the two-kernel path
+    cudaGetLastError();
+    c->fused_clusters = 0;
+  } else if (gpos && !accumulate) {
+    CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
+  }
   LaunchArgs la = one_problem(c, L, d);
   const int items = B * K;
   {
@@ -303,6 +339,7 @@ static int create_impl(const ptycho_geom* geom, int32_t max_batch, size_t scratc
   c->res_fwd = c->ops->resident_clusters(false, false);
   c->slots = c->ops->resident_clusters(true, false);
   c->res_adj = c->ops->resident_clusters(true, true);
+  c->fused_clusters = std::min(c->slots, c->ops->resident_fused());
   // waves mode
   const Layout Ls = make_layout(c->g, max_batch, true, 0);
   const Layout Lr = make_layout(c->g, max_batch, false, external_slots ? 0 : c->slots);
@@ -551,6 +588,8 @@ int ptycho_check(ptycho_ctx* c, ptycho_stream stream) {
   unsigned st = 0;
   CK(cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
   CK(cudaMemset(c->status, 0, sizeof(unsigned)));
+  if (st & ptycho::PTYCHO_STATUS_TIMEOUT)
+    return perr(PTYCHO_ETIMEDOUT, "a bounded device wait ran out; the last gradients are not valid");
   if (st & ptycho::PTYCHO_STATUS_OUT_OF_BOUNDS)
     return perr(PTYCHO_EOUTOFBOUNDS, "a scan window left the object; its item was skipped");
   return PTYCHO_OK;

@@ -7,6 +7,7 @@ namespace ptycho {
 
 constexpr int kMaxDesc = 16;           // problems per batched launch
 constexpr unsigned PTYCHO_STATUS_OUT_OF_BOUNDS = 1u;
+constexpr unsigned PTYCHO_STATUS_TIMEOUT = 2u;     // a bounded device wait ran out
 
 // One problem (dataset) inside a launch.  All pointers are device pointers.
 struct ProblemDesc {
@@ -34,6 +35,18 @@ struct LaunchArgs {
   unsigned* status;         // device status word (PTYCHO_STATUS_*)
   float2* slots;            // recompute scratch, one slot per cluster
   long long slot_stride;    // float2 per slot
+};
+
+// Extra arguments of the fused loss + adjoint kernel (entry waves
+// recomputed; the K mode clusters of a position meet once per position).
+struct FusedArgs {
+  const float* Iexp;   // [npos][NP] measured patterns, natural order
+  float* Ibuf;         // [B][K][NP] per-mode far-field intensity, slot order
+  unsigned* cnt;       // [B] CTAs that published their intensity (zeroed per launch)
+  double* lpart;       // [B] loss per position (zeroed per launch)
+  int model;           // noise model
+  float eps, c;
+  int groups;          // positions per round = clusters / K
 };
 
 }  // namespace ptycho

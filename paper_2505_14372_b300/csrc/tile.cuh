@@ -357,9 +357,9 @@ struct Tile {
   // Column contiguous stage on the spectral side.  Values come from the slots
   // (FROM_SMEM) or load(pu, pv); FWD applies the forward s2 so that register
   // i holds spectral slot pu = R2 k1 + i; op(pu, pv, v) is the pointwise
-  // product; INV applies inverse s2' + twiddle and writes back in place.
-  // The caller synchronises.
-  template <bool FROM_SMEM, bool FWD, bool INV, class Load, class Op>
+  // product; INV applies inverse s2' + twiddle and writes back in place; WB
+  // (without INV) writes the spectral values back.  The caller synchronises.
+  template <bool FROM_SMEM, bool FWD, bool INV, bool WB = false, class Load, class Op>
   __device__ static void col_contig(float2* wave, const float2* twC, int rank, const Load& load,
                                     const Op& op) {
 #pragma unroll 1
@@ -385,6 +385,9 @@ struct Tile {
         Dft<R2, +1>::run(x);
 #pragma unroll
         for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
+#pragma unroll
+        for (int i = 0; i < R2; ++i) wave[cslot(rank, b, r0 + i, cc)] = x[i];
+      } else if constexpr (WB) {
 #pragma unroll
         for (int i = 0; i < R2; ++i) wave[cslot(rank, b, r0 + i, cc)] = x[i];
       }

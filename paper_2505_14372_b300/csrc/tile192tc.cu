@@ -125,6 +125,10 @@ struct TcEngine {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
     return e != cudaSuccess ? e : E::adjoint(L, clusters, store, s);
   }
+  static cudaError_t adjoint_fused(const LaunchArgs& L, const FusedArgs& F, int clusters, cudaStream_t s) {
+    cudaError_t e = ensure_tables(TL::R1, TL::R2);
+    return e != cudaSuccess ? e : E::adjoint_fused(L, F, clusters, s);
+  }
   static cudaError_t probe_grad(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s) {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
     return e != cudaSuccess ? e : E::probe_grad(gPhat, gP, K, acc, s);
@@ -140,6 +144,7 @@ struct TcEngine {
       x.forward = &forward;
       x.adjoint = &adjoint;
       x.probe_grad = &probe_grad;
+      x.adjoint_fused = &adjoint_fused;
       x.fft_debug = &fft_debug;
       return x;
     }();

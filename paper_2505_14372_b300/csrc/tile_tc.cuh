@@ -165,7 +165,7 @@ struct TileTC : Base {
   }
 
   // ---- column contiguous (spectral side) --------------------------------
-  template <bool FROM_SMEM, bool FWD, bool INV, class Load, class Op>
+  template <bool FROM_SMEM, bool FWD, bool INV, bool WB = false, class Load, class Op>
   __device__ static void col_contig(float2* wave, const float2* twC, int rank, const Load& load, const Op& op) {
     const int warp = threadIdx.x >> 5;
     TcMat<MODE> Mf, Mi;
@@ -193,6 +193,7 @@ struct TileTC : Base {
                 int pu, pv;
                 pu_pv(id, m, pu, pv);
                 op(pu, pv, v);
+                if constexpr (WB) wave[sl(id, m)] = v;
               }
             });
         if constexpr (INV) __syncwarp();
