@@ -18,8 +18,7 @@ What it computes (arXiv 2505.14372):
     (Wirtinger calculus), for all slices and modes at once, and the Adam
     update applied to it.
 
-Readings taken where the paper is silent or ambiguous (each one is also
-listed in DESIGN.md):
+Readings taken where the paper is silent or ambiguous:
   R1  S slices take S-1 propagations; nothing is propagated after the last.
   R2  F is the unnormalised DFT with kernel exp(-2 pi i k x / N); F^-1 carries
       1/N; the far field uses the orthonormal F/sqrt(N); no fftshift: the
@@ -56,6 +55,18 @@ listed in DESIGN.md):
       probe L2 lambda sum |P|^2, in-plane Tikhonov lambda sum of squared
       forward differences along y and x inside each slice, and Tikhonov
       across layers lambda sum_s |O_{s+1} - O_s|^2.
+  R12 Reduced-precision wavefields (§2.2 names 16-bit formats as future
+      work): the entry waves that the backward pass reads for the object
+      gradient may be stored as binary16 or bfloat16, rounded to nearest
+      even from their binary32 values; nothing else is rounded.
+  R13 ePIE / 3PIE (§3.3.1): the group's positions are updated together
+      from the same O and P; the object normaliser max|O_s|^2 is taken over
+      the whole slice and the wave normaliser max|psi_s|^2 per position and
+      mode (the paper writes both per slice); between slices the update of
+      the incident wave is carried back to the previous exit plane by the
+      adjoint propagator conj(H); the probe update of each mode is the
+      group mean of the unshifted entry-plane updates (the paper's mean is
+      over the group); c and eps are the noise model's.
 """
 from __future__ import annotations
 
@@ -75,6 +86,7 @@ __all__ = [
     "shift_probe", "bandlimit_mask", "propagator", "propagate",
     "forward", "forward_waves", "loss_terms", "loss_value", "gradient",
     "adam_update", "step", "position_gradient", "vjp", "GAUSSIAN", "regularizers",
+    "round_storage", "epie_update",
 ]
 
 
@@ -293,11 +305,42 @@ def _backprop(O, psis, A, n, d, seeds, g: Geom):
     return gO, idft2(gPhat)
 
 
-def gradient(O, P, pos, I_exp, g: Geom):
+def round_storage(z, fmt):
+    """Complex array as held in a reduced storage format (R12), real and
+    imaginary parts separately: first rounded to binary32 (the precision the
+    kernels compute in), then to nearest with ties to even on
+    'f16' - IEEE binary16 (11 significant bits, subnormals below 2^-14),
+    'bf16' - bfloat16 (the upper 16 bits of binary32: 8 significant bits).
+    None or 'f32' keeps binary32."""
+    z = np.asarray(z, dtype=np.complex128)
+
+    def part(x):
+        x32 = np.asarray(x, dtype=np.float32)
+        if fmt in (None, "f32"):
+            return x32.astype(np.float64)
+        if fmt == "f16":
+            return x32.astype(np.float16).astype(np.float64)
+        if fmt == "bf16":
+            u = x32.view(np.uint32).astype(np.uint64)
+            # add half of the dropped 16 bits, plus one when the kept part is
+            # odd (ties to even), then drop them
+            u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+            return u.astype(np.uint32).view(np.float32).astype(np.float64)
+        raise ValueError("unknown storage format")
+
+    return part(z.real) + 1j * part(z.imag)
+
+
+def gradient(O, P, pos, I_exp, g: Geom, wave_fmt=None):
     """Loss and its gradients (R7 convention) with respect to every object
     slice and every probe mode; the detector seed is 2 l'(I) A.
+    wave_fmt: storage format of the entry waves that the object-gradient
+    term g_O += conj(psi) g_phi reads (R12, see round_storage); the
+    propagated wavefield itself is never rounded.
     Returns (loss, gO [S,H,W], gP [K,h,w])."""
     psis, A, n, d = forward_waves(O, P, pos, g)
+    if wave_fmt is not None:
+        psis = round_storage(psis, wave_fmt)
     O = np.asarray(O, dtype=np.complex128)
     E = np.asarray(I_exp, dtype=np.float64).reshape(-1, g.h, g.w)
     seeds = np.zeros_like(A)
@@ -348,6 +391,60 @@ def position_gradient(O, P, pos, I_exp, g: Geom) -> np.ndarray:
         out[j, 0] = float(np.real(np.sum(np.conj(g_psi) * dpsi_y)))
         out[j, 1] = float(np.real(np.sum(np.conj(g_psi) * dpsi_x)))
     return out
+
+
+# ---------------------------------------------------- ePIE / 3PIE (§3.3.1)
+
+def epie_update(O, P, pos, I_exp, g: Geom, beta_O=1.0, beta_P=1.0, tiny=1e-30):
+    """One ePIE (multislice: 3PIE) update of O and P from one group of
+    positions, all of which see the same O and P (R13).  The steps, in the
+    order of §3.3.1:
+      1. detector-plane update of each mode from the generalised modulus
+         constraint of §3.1: chi(k) = (sqrt(I_exp + c) / (eps + sqrt(I + c)) - 1) A_k,
+         I the mode sum; carried to the exit plane with the inverse
+         orthonormal DFT;
+      2. for slices s = S-1 .. 0: the object update
+         dO_s = conj(psi_s) chi_s / max_r |psi_s|^2 (psi_s the incident
+         wave of this position and mode), then the incident-wave update
+         conj(O_s) chi_s / max_r |O_s|^2 (maximum over the whole slice),
+         propagated back to the exit plane of slice s-1 with conj(H);
+      3. the probe-plane update is unshifted (conjugate Fourier ramp);
+         object updates are summed over modes and positions, probe updates
+         averaged over the positions:
+         O += beta_O sum dO, P_k += beta_P mean_j unshift(chi_0).
+    The noise model must be the amplitude one (c = 0 ePIE, c = 3/8
+    Anscombe).  Returns (O_new, P_new, loss) with the group's amplitude loss
+    before the update."""
+    if g.loss != AMPLITUDE:
+        raise ValueError("ePIE uses the amplitude / Anscombe modulus update")
+    psis, A, n, d = forward_waves(O, P, pos, g)
+    O = np.asarray(O, dtype=np.complex128)
+    P = np.asarray(P, dtype=np.complex128)
+    E = np.asarray(I_exp, dtype=np.float64).reshape(-1, g.h, g.w)
+    Hs = _props(g)
+    B = n.shape[0]
+    inv_omax = [1.0 / max(float(np.max(np.abs(O[s]) ** 2)), tiny) for s in range(g.S)]
+    dO = np.zeros_like(O)
+    dPhat = np.zeros((g.K, g.h, g.w), dtype=np.complex128)
+    loss = 0.0
+    for j in range(B):
+        I = np.sum(np.abs(A[j]) ** 2, axis=0)
+        loss += float(np.sum(loss_terms(I, E[j], g)[0]))
+        m = np.sqrt(E[j] + g.c) / (g.eps + np.sqrt(I + g.c)) - 1.0
+        y0, x0 = n[j]
+        for k in range(g.K):
+            chi = idft2_ortho(m * A[j, k])
+            for s in range(g.S - 1, -1, -1):
+                psi = psis[j, s, k]
+                pmax = max(float(np.max(np.abs(psi) ** 2)), tiny)
+                dO[s, y0:y0 + g.h, x0:x0 + g.w] += np.conj(psi) * chi / pmax
+                chi = inv_omax[s] * np.conj(_patch(O, s, n[j], g.h, g.w)) * chi
+                if s > 0:
+                    chi = idft2(np.conj(Hs[s - 1]) * dft2(chi))
+            dPhat[k] += np.conj(shift_ramp(d[j, 0], d[j, 1], g.h, g.w)) * dft2(chi)
+    O_new = O + beta_O * dO
+    P_new = P + beta_P * idft2(dPhat) / max(B, 1)
+    return O_new, P_new, loss
 
 
 # ---------------------------------------------------- regularisers (§3.4)
