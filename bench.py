@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3])
     ap.add_argument("--waves", default="recompute", choices=["recompute", "store"])
+    ap.add_argument("--wave-prec", default="f32", choices=["f32", "f16", "bf16"],
+                    help="storage format of the entry-wave copies read by the object gradient")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--dft", default="fft", choices=["fft", "tf32x3", "bf16x3", "tf32"],
                     help="DFT evaluation inside the tile (tensor-core variants: 192x192 window)")
@@ -121,15 +123,15 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def workload_geometry(wl, waves, dft="fft"):
+def workload_geometry(wl, waves, dft="fft", wave_prec="f32"):
     from paper_2505_14372_b300 import Geometry
     return Geometry(S=wl.S, K=wl.K, N=wl.N, H=wl.H, W=wl.W, dx=wl.dx, lam=wl.lam, dz=wl.dz,
                     bandlimit=wl.bandlimit, loss={0: "amplitude", 1: "poisson"}[wl.loss],
-                    eps=wl.eps, c=wl.c, waves=waves, dft=dft)
+                    eps=wl.eps, c=wl.c, waves=waves, dft=dft, wave_prec=wave_prec)
 
 
-def config_dict(wl, waves, dft="fft"):
-    return {"workload": wl.name, "dft": dft, "slices": wl.S, "modes": wl.K, "window": wl.N, "object": [wl.H, wl.W],
+def config_dict(wl, waves, dft="fft", wave_prec="f32"):
+    return {"workload": wl.name, "dft": dft, "wave_storage": wave_prec, "slices": wl.S, "modes": wl.K, "window": wl.N, "object": [wl.H, wl.W],
             "positions": wl.P, "group": wl.B, "loss": {0: "amplitude", 1: "poisson"}[wl.loss],
             "waves": waves, "grouping": "sparse, reshuffled every pass",
             "l2": "inputs larger than L2 (patterns %.1f GB, object %.0f MB) - no flush" % (
@@ -383,7 +385,7 @@ def main():
     if args.group:
         import dataclasses
         wl = dataclasses.replace(wl, B=args.group)
-    geom = workload_geometry(wl, args.waves, args.dft)
+    geom = workload_geometry(wl, args.waves, args.dft, args.wave_prec)
     B = wl.B
 
     # ---- inputs resident in HBM
@@ -479,7 +481,7 @@ def main():
     if os.path.exists(traffic_path):
         with open(traffic_path) as f:
             tj = json.load(f)
-        key = f"{dom}/{args.workload}/{args.waves}"
+        key = f"{dom}/{args.workload}/{args.waves}/{args.wave_prec}"
         # counters are only valid for the kernel source they were taken on
         if key in tj and tj[key].get("kernel_source") == kernel_source_hash():
             traffic = tj[key]["bytes_per_item"] * B * wl.K
@@ -495,7 +497,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "positions/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_dict(wl, args.waves, args.dft), "roofline": roofline, "e2e": e2e,
+                "config": config_dict(wl, args.waves, args.dft, args.wave_prec), "roofline": roofline, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "last_stats": loss_last}
         if world == 1 and not args.no_baseline:
             n_s = 8 if wl.S > 1 else 64

@@ -84,6 +84,15 @@ typedef enum { PTYCHO_WAVES_AUTO = 0, PTYCHO_WAVES_STORE = 1, PTYCHO_WAVES_RECOM
  * The tensor-core variants exist for the 192 x 192 window. */
 typedef enum { PTYCHO_DFT_FFT = 0, PTYCHO_DFT_TF32X3 = 1, PTYCHO_DFT_BF16X3 = 2, PTYCHO_DFT_TF32 = 3 } ptycho_dft;
 
+/* Storage format of the entry waves kept between the forward pass and the
+ * object-gradient term of the adjoint (the stored array or the recompute
+ * slot): FP32, IEEE binary16 or bfloat16, each part rounded to nearest even
+ * from its FP32 value.  Only the object gradient reads these copies (the
+ * wavefield itself stays FP32 in shared memory), so intensities, loss and
+ * probe gradient are unchanged.  §2.2 names reduced-precision wavefields as
+ * the way to cut memory traffic. */
+typedef enum { PTYCHO_PREC_F32 = 0, PTYCHO_PREC_F16 = 1, PTYCHO_PREC_BF16 = 2 } ptycho_prec;
+
 /* Geometry and noise model of one reconstruction problem (§3, §3.1). */
 typedef struct {
   int32_t S, K;       /* slices, incoherent probe modes (K >= 1, S >= 1) */
@@ -99,6 +108,7 @@ typedef struct {
   double c;           /* amplitude-model offset (0 amplitude, 3/8 Anscombe) */
   int32_t waves;      /* ptycho_waves */
   int32_t dft;        /* ptycho_dft: how the 2-D DFTs are evaluated */
+  int32_t wave_prec;  /* ptycho_prec: storage of the entry waves */
 } ptycho_geom;
 
 typedef struct ptycho_ctx ptycho_ctx;
@@ -171,12 +181,16 @@ int ptycho_forward_static(const ptycho_geom* geom, const ptycho_c64* O, const pt
  * the weights of the cost regularisers added to the loss (§3.4; 0 = off):
  * object L2 lambda sum |O - 1|^2, in-plane Tikhonov lambda sum of squared
  * forward differences along y and x of every slice, Tikhonov across layers
- * lambda sum |O_{s+1} - O_s|^2, probe L2 lambda sum |P|^2. */
+ * lambda sum |O_{s+1} - O_s|^2, probe L2 lambda sum |P|^2, and total
+ * variation in plane (reg_obj_tv) and across layers (reg_obj_layers_tv):
+ * lambda sum (sqrt(|d|^2 + eta^2) - eta) over the same forward differences d,
+ * eta = reg_tv_eps > 0 (EINVAL otherwise when a TV weight is set). */
 typedef struct {
   float lr_O, lr_P;
   float beta1, beta2, eps;
   int32_t update_probe; /* 0: the probe is held fixed */
   float reg_obj_l2, reg_obj_tikhonov, reg_obj_layers, reg_probe_l2;
+  float reg_obj_tv, reg_obj_layers_tv, reg_tv_eps;
 } ptycho_opt;
 
 /* Adam state: first moments m (complex64), second moments v (float32, |g|^2
@@ -207,6 +221,22 @@ int ptycho_step(ptycho_ctx* ctx, ptycho_c64* O, ptycho_c64* P, ptycho_adam* stat
 int ptycho_step_host(ptycho_ctx* ctx, ptycho_c64* O, ptycho_c64* P, ptycho_adam* state,
                      const ptycho_opt* opt, const float* pos_host, const float* I_exp_host,
                      int32_t B, double* loss_host, double* gnorm_host, ptycho_stream stream);
+
+/* One ePIE / 3PIE update (§3.3.1) from one group of B scan positions (idx,
+ * pos_all, I_exp_all and n_pos as in ptycho_step), in place: every position
+ * of the group sees the same O and P; the detector-plane update of §3.1,
+ * chi = (sqrt(I_exp + c) / (eps + sqrt(I + c)) - 1) A, is carried back
+ * through the slices, where slice s receives conj(psi_s) chi_s /
+ * max|psi_s|^2 (per position and mode) and the incident wave
+ * conj(O_s) chi_s / max|O_s|^2 (maximum over the whole slice) is propagated
+ * back with conj(H); then O += beta_O * (sum over positions and modes) and
+ * P_k += beta_P * (mean over positions of the unshifted entry-plane
+ * update).  beta_P = 0 holds the probe.  Needs the amplitude noise model
+ * (c = 0 ePIE, c = 3/8 Anscombe), else EINVAL.  loss_out (device double,
+ * may be NULL) receives the group's amplitude loss before the update. */
+int ptycho_epie_step(ptycho_ctx* ctx, ptycho_c64* O, ptycho_c64* P, float beta_O, float beta_P,
+                     const float* pos_all, const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B,
+                     double* loss_out, ptycho_stream stream);
 
 /* Synchronises `stream` and reports (then clears) the device status word:
  * PTYCHO_EOUTOFBOUNDS if any item was skipped since the last check. */

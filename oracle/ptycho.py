@@ -18,7 +18,8 @@ What it computes (arXiv 2505.14372):
     (Wirtinger calculus), for all slices and modes at once, and the Adam
     update applied to it.
 
-Readings taken where the paper is silent or ambiguous:
+Readings taken where the paper is silent or ambiguous (numbered as in the
+repository's list of readings):
   R1  S slices take S-1 propagations; nothing is propagated after the last.
   R2  F is the unnormalised DFT with kernel exp(-2 pi i k x / N); F^-1 carries
       1/N; the far field uses the orthonormal F/sqrt(N); no fftshift: the
@@ -35,31 +36,36 @@ Readings taken where the paper is silent or ambiguous:
       top-left corner.  n = floor(r + 1/2) picks the object patch and
       delta = r - n in [-1/2, 1/2) is applied as the Fourier phase ramp
       exp(-2 pi i (f_u delta_y / h + f_v delta_x / w)), i.e. P(r - delta).
-  R5  Amplitude (c = 0) / Anscombe (c = 3/8) loss per pixel:
+  R5/R6 Amplitude (c = 0) / Anscombe (c = 3/8) loss per pixel:
       l = 1/2 (sqrt(I + c + eps) - sqrt(I_exp + c + eps))^2.
       Poisson loss per pixel: l = I - I_exp - I_exp (log(I+eps) - log(I_exp+eps)),
       whose derivative 1 - I_exp/(I + eps) is exactly the paper's Poisson
       detector gradient factor.
-  R6  The loss is the plain sum over pixels and positions.
   R7  Gradient of a real L with respect to complex z is
       dL/dRe z + i dL/dIm z (= 2 dL/d conj(z)), twice the paper's
       conj(dL/dz); it matches finite differences on Re and Im directly.
   R8  Complex Adam: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2)|g|^2 (real),
       z <- z - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps_adam).
   R9  Incoherent mode weights are carried by the mode amplitudes.
-  R10 Gaussian noise model (§3.1): l = (I - I_exp)^2 / (2 sigma^2), the
+  R10 The loss is the plain sum over pixels and positions.
+  R13 Gaussian noise model (§3.1): l = (I - I_exp)^2 / (2 sigma^2), the
       normalisation constant dropped; sigma is passed in the c field.
-  R11 Cost regularisers (§3.4) act on the complex transmission and the probe
+  R14 Cost regularisers (§3.4) act on the complex transmission and the probe
       (the paper names the phase; for weak phase objects |grad O|^2 is
       |grad phase|^2): object L2 lambda sum |O - 1|^2 (vacuum is O = 1),
       probe L2 lambda sum |P|^2, in-plane Tikhonov lambda sum of squared
       forward differences along y and x inside each slice, and Tikhonov
       across layers lambda sum_s |O_{s+1} - O_s|^2.
-  R12 Reduced-precision wavefields (§2.2 names 16-bit formats as future
+      TV regularisers (§3.4, in-plane and across layers) act on the complex
+      transmission like the Tikhonov ones, with the absolute value of each
+      forward difference d smoothed to sqrt(|d|^2 + eta^2) - eta (eta > 0,
+      the paper gives no smoothing; without one the gradient is undefined
+      at d = 0).
+  R15 Reduced-precision wavefields (§2.2 names 16-bit formats as future
       work): the entry waves that the backward pass reads for the object
       gradient may be stored as binary16 or bfloat16, rounded to nearest
       even from their binary32 values; nothing else is rounded.
-  R13 ePIE / 3PIE (§3.3.1): the group's positions are updated together
+  R16 ePIE / 3PIE (§3.3.1): the group's positions are updated together
       from the same O and P; the object normaliser max|O_s|^2 is taken over
       the whole slice and the wave normaliser max|psi_s|^2 per position and
       mode (the paper writes both per slice); between slices the update of
@@ -262,7 +268,7 @@ def forward(O, P, pos, g: Geom) -> np.ndarray:
 # ----------------------------------------------------------- loss (§3.1)
 
 def loss_terms(I, I_exp, g: Geom):
-    """Per-pixel loss l(I) and its derivative dl/dI (R5)."""
+    """Per-pixel loss l(I) and its derivative dl/dI (R5/R6, R13)."""
     I = np.asarray(I, dtype=np.float64)
     E = np.asarray(I_exp, dtype=np.float64)
     if g.loss == AMPLITUDE:
@@ -306,7 +312,7 @@ def _backprop(O, psis, A, n, d, seeds, g: Geom):
 
 
 def round_storage(z, fmt):
-    """Complex array as held in a reduced storage format (R12), real and
+    """Complex array as held in a reduced storage format (R15), real and
     imaginary parts separately: first rounded to binary32 (the precision the
     kernels compute in), then to nearest with ties to even on
     'f16' - IEEE binary16 (11 significant bits, subnormals below 2^-14),
@@ -335,7 +341,7 @@ def gradient(O, P, pos, I_exp, g: Geom, wave_fmt=None):
     """Loss and its gradients (R7 convention) with respect to every object
     slice and every probe mode; the detector seed is 2 l'(I) A.
     wave_fmt: storage format of the entry waves that the object-gradient
-    term g_O += conj(psi) g_phi reads (R12, see round_storage); the
+    term g_O += conj(psi) g_phi reads (R15, see round_storage); the
     propagated wavefield itself is never rounded.
     Returns (loss, gO [S,H,W], gP [K,h,w])."""
     psis, A, n, d = forward_waves(O, P, pos, g)
@@ -397,7 +403,7 @@ def position_gradient(O, P, pos, I_exp, g: Geom) -> np.ndarray:
 
 def epie_update(O, P, pos, I_exp, g: Geom, beta_O=1.0, beta_P=1.0, tiny=1e-30):
     """One ePIE (multislice: 3PIE) update of O and P from one group of
-    positions, all of which see the same O and P (R13).  The steps, in the
+    positions, all of which see the same O and P (R16).  The steps, in the
     order of §3.3.1:
       1. detector-plane update of each mode from the generalised modulus
          constraint of §3.1: chi(k) = (sqrt(I_exp + c) / (eps + sqrt(I + c)) - 1) A_k,
@@ -449,8 +455,9 @@ def epie_update(O, P, pos, I_exp, g: Geom, beta_O=1.0, beta_P=1.0, tiny=1e-30):
 
 # ---------------------------------------------------- regularisers (§3.4)
 
-def regularizers(O, P, l2_obj=0.0, tikhonov=0.0, layers=0.0, l2_probe=0.0):
-    """Cost-regulariser value and gradients (R7 convention) (R11)."""
+def regularizers(O, P, l2_obj=0.0, tikhonov=0.0, layers=0.0, l2_probe=0.0, tv=0.0, tv_layers=0.0,
+                 tv_eps=1e-3):
+    """Cost-regulariser value and gradients (R7 convention) (R14)."""
     O = np.asarray(O, dtype=np.complex128)
     P = np.asarray(P, dtype=np.complex128)
     val = 0.0
@@ -475,6 +482,26 @@ def regularizers(O, P, l2_obj=0.0, tikhonov=0.0, layers=0.0, l2_probe=0.0):
         val += layers * float(np.sum(np.abs(dz) ** 2))
         gO[1:] += 2.0 * layers * dz
         gO[:-1] -= 2.0 * layers * dz
+
+    def tv_term(lam, d):
+        # lam sum (sqrt(|d|^2 + eta^2) - eta); its R7 gradient with respect to
+        # the minuend of d is lam d / sqrt(|d|^2 + eta^2)
+        r = np.sqrt(np.abs(d) ** 2 + tv_eps ** 2)
+        return lam * float(np.sum(r - tv_eps)), lam * d / r
+
+    if tv:
+        v1, t1 = tv_term(tv, O[:, 1:, :] - O[:, :-1, :])
+        v2, t2 = tv_term(tv, O[:, :, 1:] - O[:, :, :-1])
+        val += v1 + v2
+        gO[:, 1:, :] += t1
+        gO[:, :-1, :] -= t1
+        gO[:, :, 1:] += t2
+        gO[:, :, :-1] -= t2
+    if tv_layers and O.shape[0] > 1:
+        v3, t3 = tv_term(tv_layers, O[1:] - O[:-1])
+        val += v3
+        gO[1:] += t3
+        gO[:-1] -= t3
     return val, gO, gP
 
 

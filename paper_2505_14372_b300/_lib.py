@@ -27,13 +27,15 @@ class Geom(C.Structure):
     _fields_ = [("S", C.c_int32), ("K", C.c_int32), ("h", C.c_int32), ("w", C.c_int32),
                 ("H", C.c_int32), ("W", C.c_int32), ("dx", C.c_double), ("lam", C.c_double),
                 ("dz", C.POINTER(C.c_double)), ("bandlimit", C.c_double), ("loss", C.c_int32),
-                ("eps", C.c_double), ("c", C.c_double), ("waves", C.c_int32), ("dft", C.c_int32)]
+                ("eps", C.c_double), ("c", C.c_double), ("waves", C.c_int32), ("dft", C.c_int32),
+                ("wave_prec", C.c_int32)]
 
 
 class Opt(C.Structure):
     _fields_ = [("lr_O", C.c_float), ("lr_P", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("update_probe", C.c_int32), ("reg_obj_l2", C.c_float),
-                ("reg_obj_tikhonov", C.c_float), ("reg_obj_layers", C.c_float), ("reg_probe_l2", C.c_float)]
+                ("reg_obj_tikhonov", C.c_float), ("reg_obj_layers", C.c_float), ("reg_probe_l2", C.c_float),
+                ("reg_obj_tv", C.c_float), ("reg_obj_layers_tv", C.c_float), ("reg_tv_eps", C.c_float)]
 
 
 class Adam(C.Structure):
@@ -79,6 +81,7 @@ SIGNATURES = {
     "ptycho_step": (I32, [P_, P_, P_, C.POINTER(Adam), C.POINTER(Opt), P_, P_, I32, P_, I32, P_, P_]),
     "ptycho_step_host": (I32, [P_, P_, P_, C.POINTER(Adam), C.POINTER(Opt), P_, P_, I32,
                                C.POINTER(C.c_double), C.POINTER(C.c_double), P_]),
+    "ptycho_epie_step": (I32, [P_, P_, P_, C.c_float, C.c_float, P_, P_, I32, P_, I32, P_, P_]),
     "ptycho_check": (I32, [P_, P_]),
     "ptycho_make_groups": (I32, [I32, I32, C.c_uint64, C.c_int64, I32, P_, P_]),
     "ptycho_set_timing": (I32, [P_, I32]),

@@ -18,6 +18,7 @@ from ._lib import check, lib
 LOSS = {"amplitude": 0, "anscombe": 0, "poisson": 1, "gaussian": 2}
 WAVES = {"auto": 0, "store": 1, "recompute": 2}
 DFT = {"fft": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3}
+PREC = {"f32": 0, "f16": 1, "bf16": 2}
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
@@ -51,19 +52,22 @@ class Geometry:
     c: float = 0.0
     waves: str = "auto"
     dft: str = "fft"
+    wave_prec: str = "f32"
 
     def to_c(self):
         dz = (C.c_double * max(len(self.dz), 1))(*self.dz) if len(self.dz) else None
         g = _lib.Geom(self.S, self.K, self.N, self.N, self.H, self.W, self.dx, self.lam,
                       C.cast(dz, C.POINTER(C.c_double)) if dz is not None else None,
-                      self.bandlimit, LOSS[self.loss], self.eps, self.c, WAVES[self.waves], DFT[self.dft])
+                      self.bandlimit, LOSS[self.loss], self.eps, self.c, WAVES[self.waves], DFT[self.dft],
+                      PREC[self.wave_prec])
         return g, dz
 
 
 def adam_opt(lr_O=1e-3, lr_P=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, update_probe=True, reg_obj_l2=0.0,
-             reg_obj_tikhonov=0.0, reg_obj_layers=0.0, reg_probe_l2=0.0) -> _lib.Opt:
+             reg_obj_tikhonov=0.0, reg_obj_layers=0.0, reg_probe_l2=0.0, reg_obj_tv=0.0, reg_obj_layers_tv=0.0,
+             reg_tv_eps=1e-3) -> _lib.Opt:
     return _lib.Opt(lr_O, lr_P, beta1, beta2, eps, 1 if update_probe else 0, reg_obj_l2, reg_obj_tikhonov,
-                    reg_obj_layers, reg_probe_l2)
+                    reg_obj_layers, reg_probe_l2, reg_obj_tv, reg_obj_layers_tv, reg_tv_eps)
 
 
 class AdamState:
@@ -182,6 +186,21 @@ class Context:
         check(lib().ptycho_step(self.h, _ptr(O), _ptr(P), C.byref(state.c), C.byref(opt), _ptr(pos_all),
                                 _ptr(I_exp_all), n_pos, _ptr(idx), B, _ptr(stats), _stream()))
         return stats
+
+    def epie_step(self, O, P, pos_all, I_exp_all, idx, beta_O=1.0, beta_P=1.0, loss=None):
+        """One ePIE / 3PIE update (ptycho_epie_step) of O and P in place from
+        the group idx; returns a device float64 tensor [loss before the update]."""
+        B = idx.shape[0]
+        _need(idx, torch.int32, (B,), "idx")
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float64, device=O.device)
+        g = self.geom
+        n_pos = pos_all.shape[0]
+        _need(pos_all, torch.float32, (n_pos, 2), "pos_all")
+        _need(I_exp_all, torch.float32, (n_pos, g.N, g.N), "I_exp_all")
+        check(lib().ptycho_epie_step(self.h, _ptr(O), _ptr(P), float(beta_O), float(beta_P), _ptr(pos_all),
+                                     _ptr(I_exp_all), n_pos, _ptr(idx), B, _ptr(loss), _stream()))
+        return loss
 
     def step_host(self, O, P, state: AdamState, opt, pos_host: np.ndarray, I_exp_host):
         """Step with the group's positions/patterns in host memory (numpy or

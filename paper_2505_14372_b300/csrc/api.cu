@@ -24,7 +24,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Offsets of one call's scratch inside the context arena.
 struct Layout {
-  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, cnt, waves, total;
+  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, cnt, omax, wmax, waves, total;
 };
 
 Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
@@ -47,7 +47,10 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   L.stage_pos = take((size_t)B * 2 * 4);
   L.stage_I = take((size_t)B * NP * 4);
   L.cnt = take((size_t)B * 4);
-  L.waves = take(store ? (size_t)B * g.K * g.S * NP * 8 : (size_t)slots * g.S * NP * 8);
+  L.omax = take((size_t)g.S * 4);
+  L.wmax = take((size_t)B * g.K * g.S * 4);
+  const size_t esize = g.wave_prec ? 4 : 8;  // entry-wave copies: complex64 or two 16-bit parts
+  L.waves = take(store ? (size_t)B * g.K * g.S * NP * esize : (size_t)slots * g.S * NP * esize);
   L.total = off;
   return L;
 }
@@ -76,6 +79,9 @@ int validate_geom(const ptycho_geom* g) {
   if (g->loss == PTYCHO_LOSS_AMPLITUDE && !(g->eps + g->c > 0))
     return perr(PTYCHO_EINVAL, "amplitude loss needs eps + c > 0");
   if (g->waves < 0 || g->waves > 2) return perr(PTYCHO_EINVAL, "unknown waves mode");
+  if (g->wave_prec < 0 || g->wave_prec > 2) return perr(PTYCHO_EINVAL, "unknown entry-wave storage format");
+  if (g->wave_prec != PTYCHO_PREC_F32 && g->dft != PTYCHO_DFT_FFT)
+    return perr(PTYCHO_EINVAL, "16-bit entry waves run with the FFT tile (dft = 0)");
   const double cells = (double)g->S * g->H * g->W;
   if (cells > 4.0e9) return perr(PTYCHO_EINVAL, "object too large");
   return PTYCHO_OK;
@@ -109,6 +115,7 @@ struct ptycho_ctx {
   bool store = true;
   int slots = 0;          // recompute slots (clusters of the recompute adjoint)
   int fused_clusters = 0; // resident clusters of the fused loss + adjoint kernel
+  int fused_epie = 0;     // the same for its ePIE variant
   int res_fwd = 1, res_adj = 1;
   // timing
   bool timing = false;
@@ -181,7 +188,7 @@ ProblemDesc base_desc(ptycho_ctx* c, const Layout& L, const ptycho_c64* O, const
   d.Hc = c->Hc;
   d.A = reinterpret_cast<float2*>(c->arena + L.A);
   d.w = reinterpret_cast<const float*>(c->arena + L.w);
-  d.waves = c->store ? reinterpret_cast<float2*>(c->arena + L.waves) : nullptr;
+  d.waves = c->store ? c->arena + L.waves : nullptr;
   d.gO = nullptr;
   d.gPhat = reinterpret_cast<float2*>(c->arena + L.gPhat);
   d.S = c->g.S;
@@ -201,8 +208,8 @@ LaunchArgs one_problem(ptycho_ctx* c, const Layout& L, const ProblemDesc& d) {
   a.nd = 1;
   a.total = d.B * d.K;
   a.status = c->status;
-  a.slots = reinterpret_cast<float2*>(c->arena + L.waves);
-  a.slot_stride = (long long)c->g.S * c->NP;
+  a.slots = c->arena + L.waves;
+  a.slot_stride = (long long)c->g.S * c->NP * (c->g.wave_prec ? 4 : 8);
   return a;
 }
 
@@ -221,9 +228,11 @@ int check_call(ptycho_ctx* c, int B) {
 // forward + loss + adjoint into (gO, gP); partials[0..nl) hold the loss.
 // With gI != null the seed is the external cotangent dL/dI instead of the
 // noise model's derivative (vector-Jacobian product).
+// epie: the seed is the modulus update chi and the per-slice normalisers of
+// §3.3.1 apply (gO, gP then hold the summed ePIE updates).
 int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, const int* idx, int B,
                  int npos, const float* Iexp, ptycho_c64* gO, ptycho_c64* gP, int accumulate, cudaStream_t s, int* nl_out,
-                 bool vjp = false, const float* gI = nullptr, double* gpos = nullptr) {
+                 bool vjp = false, const float* gI = nullptr, double* gpos = nullptr, bool epie = false) {
   const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
   const int K = c->g.K;
   float2* Phat = reinterpret_cast<float2*>(c->arena + L.Phat);
@@ -246,26 +255,38 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   ProblemDesc d = base_desc(c, L, O, pos, idx, B, npos);
   d.gO = reinterpret_cast<float2*>(gO);
   d.gpos = gpos;
+  const int model = epie ? ptycho::kModelEpie : c->g.loss;
+  if (epie) {
+    unsigned* omax = reinterpret_cast<unsigned*>(c->arena + L.omax);
+    d.omax = omax;
+    d.wmax = reinterpret_cast<unsigned*>(c->arena + L.wmax);
+    CK(cudaMemsetAsync(omax, 0, (size_t)c->g.S * 4, s));
+    CK(cudaMemsetAsync(d.wmax, 0, (size_t)B * K * c->g.S * 4, s));
+    Timed t(c, "slice_max", s);
+    CK(ptycho::launch_slice_absmax(reinterpret_cast<const float2*>(O), c->g.S, (long long)c->g.H * c->g.W, omax, s));
+  }
   // Entry waves recomputed: one fused loss + adjoint launch when all mode
   // clusters of a round fit on the device at once (cooperative launch).
-  if (!c->store && !vjp && c->fused_clusters >= K) {
+  const int variant = epie ? ptycho::kVarEpie : c->g.wave_prec;
+  const int fused = epie ? c->fused_epie : c->fused_clusters;
+  if (!c->store && !vjp && fused >= K) {
     if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
     ptycho::FusedArgs F{};
     F.Iexp = Iexp;
     F.Ibuf = reinterpret_cast<float*>(c->arena + L.A);
     F.cnt = reinterpret_cast<unsigned*>(c->arena + L.cnt);
     F.lpart = partials;
-    F.model = c->g.loss;
+    F.model = model;
     F.eps = (float)c->g.eps;
     F.c = (float)c->g.c;
-    F.groups = c->fused_clusters / K;
+    F.groups = fused / K;
     CK(cudaMemsetAsync(F.cnt, 0, (size_t)B * 4, s));
     CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
     LaunchArgs la = one_problem(c, L, d);
     cudaError_t e;
     {
       Timed t(c, "adjoint", s);
-      e = c->ops->adjoint_fused(la, F, F.groups * K, s);
+      e = c->ops->adjoint_fused(la, F, F.groups * K, variant, s);
     }
     if (e == cudaSuccess) {
       *nl_out = B;
@@ -275,7 +296,8 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
     }
     // the device refused the cooperative launch: take the two-kernel path
     cudaGetLastError();
-    c->fused_clusters = 0;
+    if (epie) c->fused_epie = 0;
+    else c->fused_clusters = 0;
   } else if (gpos && !accumulate) {
     CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
   }
@@ -283,20 +305,20 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   const int items = B * K;
   {
     Timed t(c, "forward", s);
-    CK(c->ops->forward(la, std::min(items, c->res_fwd), c->store, s));
+    CK(c->ops->forward(la, std::min(items, c->res_fwd), c->store, variant, s));
   }
   if (vjp) {
     Timed t(c, "seed", s);
     CK(c->ops->seed(gI, B, reinterpret_cast<float*>(c->arena + L.w), s));
   } else {
     Timed t(c, "loss", s);
-    CK(c->ops->loss(d.A, Iexp, idx, npos, B, K, c->g.loss, (float)c->g.eps, (float)c->g.c,
+    CK(c->ops->loss(d.A, Iexp, idx, npos, B, K, model, (float)c->g.eps, (float)c->g.c,
                     reinterpret_cast<float*>(c->arena + L.w), partials, nl, s));
   }
   {
     Timed t(c, "adjoint", s);
     const int cl = c->store ? std::min(items, c->res_adj) : std::min(items, c->slots);
-    CK(c->ops->adjoint(la, cl, c->store, s));
+    CK(c->ops->adjoint(la, cl, c->store, variant, s));
   }
   {
     Timed t(c, "probe_grad", s);
@@ -336,10 +358,12 @@ static int create_impl(const ptycho_geom* geom, int32_t max_batch, size_t scratc
     delete c;
     return perr(PTYCHO_ECUDA, "no CUDA device");
   }
-  c->res_fwd = c->ops->resident_clusters(false, false);
-  c->slots = c->ops->resident_clusters(true, false);
-  c->res_adj = c->ops->resident_clusters(true, true);
-  c->fused_clusters = std::min(c->slots, c->ops->resident_fused());
+  const int var = geom->wave_prec;  // kVarF32 / kVarF16 / kVarBF16
+  c->res_fwd = c->ops->resident_clusters(false, false, ptycho::kVarF32);
+  c->slots = c->ops->resident_clusters(true, false, var);
+  c->res_adj = c->ops->resident_clusters(true, true, var);
+  c->fused_clusters = std::min(c->slots, c->ops->resident_fused(var));
+  c->fused_epie = c->ops->has_variants ? std::min(c->slots, c->ops->resident_fused(ptycho::kVarEpie)) : 0;
   // waves mode
   const Layout Ls = make_layout(c->g, max_batch, true, 0);
   const Layout Lr = make_layout(c->g, max_batch, false, external_slots ? 0 : c->slots);
@@ -414,7 +438,7 @@ size_t ptycho_scratch_bytes(const ptycho_geom* geom, int32_t B, int32_t waves) {
   const EngineOps* ops = ptycho::engine_for(geom->h);
   int slots = 148 / ops->G;
   int dev;
-  if (cudaGetDevice(&dev) == cudaSuccess) slots = ops->resident_clusters(true, false);
+  if (cudaGetDevice(&dev) == cudaSuccess) slots = ops->resident_clusters(true, false, geom->wave_prec);
   else cudaGetLastError();
   return make_layout(*geom, B, waves != PTYCHO_WAVES_RECOMPUTE, slots).total;
 }
@@ -437,7 +461,7 @@ int ptycho_forward(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, cons
   LaunchArgs la = one_problem(c, L, d);
   {
     Timed t(c, "forward", s);
-    CK(c->ops->forward(la, std::min(B * c->g.K, c->res_fwd), false, s));
+    CK(c->ops->forward(la, std::min(B * c->g.K, c->res_fwd), false, ptycho::kVarF32, s));
   }
   {
     Timed t(c, "modesum", s);
@@ -510,14 +534,17 @@ static int step_impl(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
   double* stats = stats_out ? stats_out : reinterpret_cast<double*>(c->arena + L.stats);
   const long long nO = (long long)c->g.S * c->g.H * c->g.W;
   const long long nP = (long long)c->g.K * c->NP;
+  const bool tv = opt->reg_obj_tv != 0.f || opt->reg_obj_layers_tv != 0.f;
+  if (tv && !(opt->reg_tv_eps > 0.f)) return perr(PTYCHO_EINVAL, "TV regularisers need reg_tv_eps > 0");
   const bool reg = opt->reg_obj_l2 != 0.f || opt->reg_obj_tikhonov != 0.f || opt->reg_obj_layers != 0.f ||
-                   opt->reg_probe_l2 != 0.f;
+                   opt->reg_probe_l2 != 0.f || tv;
   const int nr = reg ? ptycho::kNormBlocks : 0;
   if (reg) {
     Timed t(c, "regularize", s);
     CK(ptycho::launch_regularize(reinterpret_cast<const float2*>(O), c->gO, c->g.S, c->g.H, c->g.W,
                                  reinterpret_cast<const float2*>(P), c->gP, nP, opt->reg_obj_l2,
-                                 opt->reg_obj_tikhonov, opt->reg_obj_layers, opt->reg_probe_l2, partials + nl, nr, s));
+                                 opt->reg_obj_tikhonov, opt->reg_obj_layers, opt->reg_probe_l2, opt->reg_obj_tv,
+                                 opt->reg_obj_layers_tv, opt->reg_tv_eps, partials + nl, nr, s));
   }
   {
     Timed t(c, "reduce", s);
@@ -578,6 +605,37 @@ int ptycho_step_host(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
   CK(cudaStreamSynchronize(s));
   if (loss_host) *loss_host = h[0];
   if (gnorm_host) *gnorm_host = h[1];
+  return PTYCHO_OK;
+}
+
+int ptycho_epie_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, float beta_O, float beta_P, const float* pos_all,
+                     const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B, double* loss_out,
+                     ptycho_stream stream) {
+  int rc = check_call(c, B);
+  if (rc) return rc;
+  if (!O || !P) return perr(PTYCHO_EINVAL, "NULL object or probe");
+  if (B > 0 && (!idx || !pos_all || !I_exp_all)) return perr(PTYCHO_EINVAL, "NULL positions, patterns or idx");
+  if (n_pos < 0) return perr(PTYCHO_EINVAL, "n_pos < 0");
+  if (c->g.loss != PTYCHO_LOSS_AMPLITUDE)
+    return perr(PTYCHO_EINVAL, "ePIE needs the amplitude / Anscombe noise model");
+  if (!c->ops->has_variants || c->g.wave_prec != PTYCHO_PREC_F32)
+    return perr(PTYCHO_EINVAL, "ePIE runs with the FFT tile (dft = 0) and FP32 entry waves");
+  if (!std::isfinite(beta_O) || !std::isfinite(beta_P)) return perr(PTYCHO_EINVAL, "step sizes must be finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
+  int nl = 0;
+  rc = run_gradient(c, O, P, pos_all, idx, B, n_pos, I_exp_all, reinterpret_cast<ptycho_c64*>(c->gO),
+                    reinterpret_cast<ptycho_c64*>(c->gP), 0, s, &nl, false, nullptr, nullptr, true);
+  if (rc) return rc;
+  if (loss_out) {
+    Timed t(c, "finalize", s);
+    CK(ptycho::launch_finalize(reinterpret_cast<double*>(c->arena + L.partials), nl, 0, loss_out, 0, s));
+  }
+  if (B == 0) return PTYCHO_OK;
+  Timed t(c, "epie_apply", s);
+  CK(ptycho::launch_axpy(reinterpret_cast<float2*>(O), c->gO, (long long)c->g.S * c->g.H * c->g.W, beta_O, s));
+  if (beta_P != 0.f)
+    CK(ptycho::launch_axpy(reinterpret_cast<float2*>(P), c->gP, (long long)c->g.K * c->NP, beta_P / (float)B, s));
   return PTYCHO_OK;
 }
 
@@ -658,7 +716,7 @@ size_t ctx_device_bytes(const ptycho_ctx* c) {
 
 int resident_slots(int N) {
   const EngineOps* ops = engine_for(N);
-  return ops ? ops->resident_clusters(true, false) : 0;
+  return ops ? ops->resident_clusters(true, false, kVarF32) : 0;
 }
 
 // One gradient step for several problems of the same window size: their
@@ -670,8 +728,8 @@ int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long 
   LaunchArgs la{};
   la.nd = n;
   la.status = status;
-  la.slots = slots;
-  la.slot_stride = slot_stride;
+  la.slots = reinterpret_cast<char*>(slots);
+  la.slot_stride = slot_stride * 8;
   int total = 0;
   std::vector<Layout> L(n);
   std::vector<int> nl(n);
@@ -680,7 +738,8 @@ int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long 
     ptycho_ctx* c = J.c;
     if (c->ops != ops || c->store) return perr(PTYCHO_EINVAL, "step_batch: mixed window sizes or stored waves");
     if (J.B < 1 || J.B > c->max_batch) return perr(PTYCHO_EINVAL, "step_batch: bad group size");
-    if ((long long)c->g.S * c->NP > slot_stride) return perr(PTYCHO_EINVAL, "step_batch: slot too small");
+    if ((long long)c->g.S * c->NP * (c->g.wave_prec ? 4 : 8) > slot_stride * 8)
+      return perr(PTYCHO_EINVAL, "step_batch: slot too small");
     L[i] = make_layout(c->g, c->max_batch, false, 0);
     CK(ops->probe_spectrum(J.P, reinterpret_cast<float2*>(c->arena + L[i].Phat), c->g.K, s));
     CK(cudaMemsetAsync(c->arena + L[i].gPhat, 0, (size_t)c->g.K * c->NP * 8, s));
@@ -692,7 +751,7 @@ int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long 
     la.d[i] = d;
   }
   la.total = total;
-  CK(ops->forward(la, std::min(total, jobs[0].c->res_fwd), false, s));
+  CK(ops->forward(la, std::min(total, jobs[0].c->res_fwd), false, kVarF32, s));
   for (int i = 0; i < n; ++i) {
     const StepJob& J = jobs[i];
     ptycho_ctx* c = J.c;
@@ -701,7 +760,7 @@ int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long 
                  reinterpret_cast<float*>(c->arena + L[i].w), reinterpret_cast<double*>(c->arena + L[i].partials),
                  nl[i], s));
   }
-  CK(ops->adjoint(la, std::min(total, nslots), false, s));
+  CK(ops->adjoint(la, std::min(total, nslots), false, kVarF32, s));
   for (int i = 0; i < n; ++i) {
     const StepJob& J = jobs[i];
     ptycho_ctx* c = J.c;
@@ -709,11 +768,12 @@ int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long 
     const long long nO = (long long)c->g.S * c->g.H * c->g.W, nP = (long long)c->g.K * c->NP;
     CK(ops->probe_grad(reinterpret_cast<float2*>(c->arena + L[i].gPhat), c->gP, c->g.K, 0, s));
     const bool reg = J.opt.reg_obj_l2 != 0.f || J.opt.reg_obj_tikhonov != 0.f || J.opt.reg_obj_layers != 0.f ||
-                     J.opt.reg_probe_l2 != 0.f;
+                     J.opt.reg_probe_l2 != 0.f || J.opt.reg_obj_tv != 0.f || J.opt.reg_obj_layers_tv != 0.f;
     const int nr = reg ? kNormBlocks : 0;
     if (reg)
       CK(launch_regularize(J.O, c->gO, c->g.S, c->g.H, c->g.W, J.P, c->gP, nP, J.opt.reg_obj_l2,
-                           J.opt.reg_obj_tikhonov, J.opt.reg_obj_layers, J.opt.reg_probe_l2, partials + nl[i], nr, s));
+                           J.opt.reg_obj_tikhonov, J.opt.reg_obj_layers, J.opt.reg_probe_l2, J.opt.reg_obj_tv,
+                           J.opt.reg_obj_layers_tv, J.opt.reg_tv_eps, partials + nl[i], nr, s));
     CK(launch_sumsq(c->gO, nO, partials + nl[i] + nr, kNormBlocks, s));
     CK(launch_sumsq(c->gP, nP, partials + nl[i] + nr + kNormBlocks, kNormBlocks, s));
     CK(launch_finalize(partials, nl[i] + nr, 2 * kNormBlocks, J.stats, 1, s));

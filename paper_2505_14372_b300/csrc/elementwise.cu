@@ -70,13 +70,14 @@ __global__ void k_adam(float2* __restrict__ z, float2* __restrict__ m, float* __
 // the probe: adds their gradients (dL/dRe z + i dL/dIm z) to gO / gP and
 // writes block partial sums of their value.  Object elements [0, nO), probe
 // elements [nO, nO + nP).  Object L2 penalises the distance to vacuum
-// (O = 1); Tikhonov terms use forward differences inside each slice (y, x)
-// and across layers (s).
+// (O = 1); Tikhonov (squared) and TV (smoothed modulus
+// sqrt(|d|^2 + eta^2) - eta) terms use forward differences d inside each
+// slice (y, x) and across layers (s).
 __global__ void __launch_bounds__(kRedThreads) k_regularize(const float2* __restrict__ O, float2* __restrict__ gO,
                                                             int S, int H, int W, const float2* __restrict__ P,
                                                             float2* __restrict__ gP, long long nP, float l2,
-                                                            float tik, float lay, float l2p,
-                                                            double* __restrict__ partials) {
+                                                            float tik, float lay, float l2p, float tv,
+                                                            float tvl, float eta, double* __restrict__ partials) {
   __shared__ double sh[32];
   const long long HW = (long long)H * W, nO = (long long)S * HW;
   double acc = 0.0;
@@ -121,6 +122,25 @@ __global__ void __launch_bounds__(kRedThreads) k_regularize(const float2* __rest
       if (s + 1 < S) edge(lay, e + HW, true);
       if (s > 0) edge(lay, e - HW, false);
     }
+    auto tv_edge = [&](float lam, long long nb, bool fwd) {
+      const float2 q = O[nb];
+      const float dx_ = o.x - q.x, dy_ = o.y - q.y;
+      const float r = sqrtf(dx_ * dx_ + dy_ * dy_ + eta * eta);
+      if (fwd) val += lam * (r - eta);
+      const float f = lam / r;
+      gx += f * dx_;
+      gy += f * dy_;
+    };
+    if (tv != 0.f) {
+      if (y + 1 < H) tv_edge(tv, e + W, true);
+      if (y > 0) tv_edge(tv, e - W, false);
+      if (x + 1 < W) tv_edge(tv, e + 1, true);
+      if (x > 0) tv_edge(tv, e - 1, false);
+    }
+    if (tvl != 0.f) {
+      if (s + 1 < S) tv_edge(tvl, e + HW, true);
+      if (s > 0) tv_edge(tvl, e - HW, false);
+    }
     float2 g = gO[e];
     g.x += gx;
     g.y += gy;
@@ -132,10 +152,10 @@ __global__ void __launch_bounds__(kRedThreads) k_regularize(const float2* __rest
 }
 
 cudaError_t launch_regularize(const float2* O, float2* gO, int S, int H, int W, const float2* P, float2* gP,
-                              long long nP, float l2, float tik, float lay, float l2p, double* partials, int nblocks,
-                              cudaStream_t s) {
+                              long long nP, float l2, float tik, float lay, float l2p, float tv, float tvl,
+                              float eta, double* partials, int nblocks, cudaStream_t s) {
   count_launch();
-  k_regularize<<<nblocks, kRedThreads, 0, s>>>(O, gO, S, H, W, P, gP, nP, l2, tik, lay, l2p, partials);
+  k_regularize<<<nblocks, kRedThreads, 0, s>>>(O, gO, S, H, W, P, gP, nP, l2, tik, lay, l2p, tv, tvl, eta, partials);
   return cudaGetLastError();
 }
 
@@ -158,6 +178,58 @@ cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long lo
   const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
   count_launch();
   k_adam<<<blocks, 256, 0, s>>>(z, m, v, g, n, lr, b1, b2, eps, bc1, bc2);
+  return cudaGetLastError();
+}
+
+// max |O_s|^2 of every slice (ePIE object normaliser, §3.3.1) as float
+// bits in omax[S] (zeroed by the caller): grid-stride per slice, block max,
+// one atomicMax per block.
+__global__ void k_slice_absmax(const float2* __restrict__ O, long long per_slice, unsigned* omax) {
+  __shared__ float sh[32];
+  const int s = blockIdx.y;
+  const float2* Os = O + (size_t)s * per_slice;
+  float m = 0.f;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per_slice;
+       e += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, cabs2(__ldg(Os + e)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = m;
+  __syncthreads();
+  if (warp == 0) {
+    m = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // non-negative floats order like their bit patterns
+    if (lane == 0) atomicMax(omax + s, __float_as_uint(m));
+  }
+}
+
+cudaError_t launch_slice_absmax(const float2* O, int S, long long per_slice, unsigned* omax, cudaStream_t s) {
+  if (S <= 0 || per_slice <= 0) return cudaSuccess;
+  const int bx = (int)std::max<long long>(1, std::min<long long>((per_slice + 255) / 256, (148LL * 8 + S - 1) / S));
+  count_launch();
+  k_slice_absmax<<<dim3(bx, S), 256, 0, s>>>(O, per_slice, omax);
+  return cudaGetLastError();
+}
+
+// z += a * g (the ePIE object and probe updates, §3.3.1)
+__global__ void k_axpy(float2* __restrict__ z, const float2* __restrict__ g, long long n, float a) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float2 d = __ldg(g + e);
+    float2 v = z[e];
+    v.x = fmaf(a, d.x, v.x);
+    v.y = fmaf(a, d.y, v.y);
+    z[e] = v;
+  }
+}
+
+cudaError_t launch_axpy(float2* z, const float2* g, long long n, float a, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+  count_launch();
+  k_axpy<<<blocks, 256, 0, s>>>(z, g, n, a);
   return cudaGetLastError();
 }
 

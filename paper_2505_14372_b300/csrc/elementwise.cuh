@@ -4,6 +4,7 @@
 #pragma once
 #include <stdint.h>
 
+#include "noise.cuh"
 #include "radix.cuh"
 
 namespace ptycho {
@@ -42,12 +43,9 @@ __global__ void k_modesum(const float2* __restrict__ A, float* __restrict__ I, i
   }
 }
 
-// Noise-model loss per pixel (float, cancellation-free forms) and the
-// adjoint seed weight w = 2 l'(I) / NP, in spectral slot order.
-//   amplitude/Anscombe: l = 1/2 (sqrt(I+c+eps) - sqrt(E+c+eps))^2
-//   Poisson:            l = I - E - E log((I+eps)/(E+eps))
-//   Gaussian:           l = (I - E)^2 / (2 c^2)
-// Block partial sums of l go to partials[blockIdx.x] in FP64.
+// Noise-model loss per pixel (noise.cuh) and the adjoint seed weight
+// w = 2 l'(I) / NP, in spectral slot order.  Block partial sums of l go to
+// partials[blockIdx.x] in FP64.
 template <class TL>
 __global__ void __launch_bounds__(kRedThreads) k_loss(const float2* __restrict__ A, const float* __restrict__ Iexp,
                                                       const int* __restrict__ idx, int npos, int B, int K,
@@ -73,20 +71,7 @@ __global__ void __launch_bounds__(kRedThreads) k_loss(const float2* __restrict__
     for (int k = 0; k < K; ++k) I += cabs2(__ldg(a + (size_t)k * TL::NP));
     I *= 1.0f / (float)TL::NP;
     float l, dl;
-    if (model == 0) {
-      const float sa = sqrtf(I + c + eps), sb = sqrtf(E + c + eps);
-      const float diff = (I - E) / (sa + sb);
-      l = 0.5f * diff * diff;
-      dl = 0.5f * (1.0f - sb / sa);
-    } else if (model == 1) {
-      const float d = (I - E) / (E + eps);
-      l = (I - E) - E * log1pf(d);
-      dl = 1.0f - E / (I + eps);
-    } else {  // Gaussian, c = sigma
-      const float r = (I - E) / (c * c);
-      l = 0.5f * r * (I - E);
-      dl = r;
-    }
+    noise_model(model, eps, c, I, E, l, dl);
     w[e] = 2.0f * dl * (1.0f / (float)TL::NP);
     acc += (double)l;
   }

@@ -10,8 +10,10 @@ struct EngineOps {
   int N, G, T, R1, R2;
   size_t smem;
   cudaError_t (*probe_spectrum)(const float2* P, float2* Phat, int K, cudaStream_t s);
-  cudaError_t (*forward)(const LaunchArgs& L, int clusters, bool store, cudaStream_t s);
-  cudaError_t (*adjoint)(const LaunchArgs& L, int clusters, bool store, cudaStream_t s);
+  // variant: Variant (launch.h); engines without all variants return
+  // cudaErrorNotSupported for the others (see has_variants)
+  cudaError_t (*forward)(const LaunchArgs& L, int clusters, bool store, int variant, cudaStream_t s);
+  cudaError_t (*adjoint)(const LaunchArgs& L, int clusters, bool store, int variant, cudaStream_t s);
   cudaError_t (*probe_grad)(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s);
   cudaError_t (*fft_debug)(const float2* in, float2* out, int count, int dir, cudaStream_t s);
   cudaError_t (*modesum)(const float2* A, float* I, int B, int K, cudaStream_t s);
@@ -19,10 +21,11 @@ struct EngineOps {
                       float eps, float c, float* w, double* partials, int nblocks, cudaStream_t s);
   cudaError_t (*seed)(const float* gI, int B, float* w, cudaStream_t s);
   // fused loss + adjoint (cooperative cluster launch of `clusters` clusters)
-  cudaError_t (*adjoint_fused)(const LaunchArgs& L, const FusedArgs& F, int clusters, cudaStream_t s);
-  int (*resident_fused)();
+  cudaError_t (*adjoint_fused)(const LaunchArgs& L, const FusedArgs& F, int clusters, int variant, cudaStream_t s);
+  int (*resident_fused)(int variant);
   // resident clusters of the forward / adjoint kernels on the current device
-  int (*resident_clusters)(bool adjoint, bool store);
+  int (*resident_clusters)(bool adjoint, bool store, int variant);
+  bool has_variants;  // reduced-precision waves and ePIE are instantiated
 };
 
 const EngineOps* engine_64();
@@ -49,10 +52,12 @@ cudaError_t launch_sumsq(const float2* g, long long n, double* partials, int nbl
 cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out, int sqrt_second,
                             cudaStream_t s);
 cudaError_t launch_regularize(const float2* O, float2* gO, int S, int H, int W, const float2* P, float2* gP,
-                              long long nP, float l2, float tik, float lay, float l2p, double* partials, int nblocks,
-                              cudaStream_t s);
+                              long long nP, float l2, float tik, float lay, float l2p, float tv, float tvl,
+                              float eta, double* partials, int nblocks, cudaStream_t s);
 cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long long n, float lr, float b1,
                         float b2, float eps, float bc1, float bc2, cudaStream_t s);
+cudaError_t launch_slice_absmax(const float2* O, int S, long long per_slice, unsigned* omax, cudaStream_t s);
+cudaError_t launch_axpy(float2* z, const float2* g, long long n, float a, cudaStream_t s);
 
 // process-wide count of kernels this library has launched (engine_impl /
 // elementwise launchers bump it once per launch)

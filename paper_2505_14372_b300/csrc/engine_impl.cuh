@@ -1,6 +1,7 @@
 // Launchers of one tile shape; included once per window size.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "elementwise.cuh"
 #include "engine.h"
@@ -8,8 +9,26 @@
 
 namespace ptycho {
 
-template <class TL>
+// ALLV: instantiate every Variant (otherwise FP32 gradient kernels only).
+template <class TL, bool ALLV = true>
 struct Engine {
+  // calls f(std::integral_constant<int, V>) for the runtime variant
+  template <class F>
+  static cudaError_t with_variant(int variant, const F& f) {
+    if constexpr (ALLV) {
+      switch (variant) {
+        case kVarF32: return f(std::integral_constant<int, kVarF32>{});
+        case kVarF16: return f(std::integral_constant<int, kVarF16>{});
+        case kVarBF16: return f(std::integral_constant<int, kVarBF16>{});
+        case kVarEpie: return f(std::integral_constant<int, kVarEpie>{});
+        default: return cudaErrorNotSupported;
+      }
+    } else {
+      if (variant != kVarF32) return cudaErrorNotSupported;
+      return f(std::integral_constant<int, kVarF32>{});
+    }
+  }
+
   template <class K>
   static cudaError_t launch(K kernel, int clusters, cudaStream_t s, auto... args) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM);
@@ -96,13 +115,18 @@ struct Engine {
   static cudaError_t probe_spectrum(const float2* P, float2* Phat, int K, cudaStream_t s) {
     return launch(k_probe_spectrum<TL>, K, s, P, Phat, K);
   }
-  static cudaError_t forward(const LaunchArgs& L, int clusters, bool store, cudaStream_t s) {
-    if (store) return launch(k_forward<TL, true>, clusters, s, L);
-    return launch(k_forward<TL, false>, clusters, s, L);
+  static cudaError_t forward(const LaunchArgs& L, int clusters, bool store, int variant, cudaStream_t s) {
+    // without stored waves the forward writes the far field only (the
+    // recomputing adjoint records what ePIE needs itself)
+    if (!store) return launch(k_forward<TL, false, kVarF32>, clusters, s, L);
+    return with_variant(variant, [&](auto v) { return launch(k_forward<TL, true, decltype(v)::value>, clusters, s, L); });
   }
-  static cudaError_t adjoint(const LaunchArgs& L, int clusters, bool store, cudaStream_t s) {
-    if (store) return launch(k_adjoint<TL, true>, clusters, s, L);
-    return launch(k_adjoint<TL, false>, clusters, s, L);
+  static cudaError_t adjoint(const LaunchArgs& L, int clusters, bool store, int variant, cudaStream_t s) {
+    return with_variant(variant, [&](auto v) {
+      constexpr int V = decltype(v)::value;
+      if (store) return launch(k_adjoint<TL, true, V>, clusters, s, L);
+      return launch(k_adjoint<TL, false, V>, clusters, s, L);
+    });
   }
   static cudaError_t probe_grad(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s) {
     return launch(k_probe_grad<TL>, K, s, gPhat, gP, K, acc);
@@ -131,20 +155,35 @@ struct Engine {
     k_seed<TL><<<blocks, 256, 0, s>>>(gI, B, w);
     return cudaGetLastError();
   }
-  static cudaError_t adjoint_fused(const LaunchArgs& L, const FusedArgs& F, int clusters, cudaStream_t s) {
-    return launch_coop(k_adjoint_fused<TL>, clusters, s, L, F);
+  static cudaError_t adjoint_fused(const LaunchArgs& L, const FusedArgs& F, int clusters, int variant,
+                                   cudaStream_t s) {
+    return with_variant(variant,
+                        [&](auto v) { return launch_coop(k_adjoint_fused<TL, decltype(v)::value>, clusters, s, L, F); });
   }
-  static int resident_fused() { return resident(k_adjoint_fused<TL>); }
-  static int resident_clusters(bool adj, bool store) {
-    if (adj) return store ? resident(k_adjoint<TL, true>) : resident(k_adjoint<TL, false>);
-    return store ? resident(k_forward<TL, true>) : resident(k_forward<TL, false>);
+  static int resident_fused(int variant) {
+    int n = 0;
+    with_variant(variant, [&](auto v) {
+      n = resident(k_adjoint_fused<TL, decltype(v)::value>);
+      return cudaSuccess;
+    });
+    return n;
+  }
+  static int resident_clusters(bool adj, bool store, int variant) {
+    int n = 0;
+    with_variant(variant, [&](auto v) {
+      constexpr int V = decltype(v)::value;
+      if (adj) n = store ? resident(k_adjoint<TL, true, V>) : resident(k_adjoint<TL, false, V>);
+      else n = store ? resident(k_forward<TL, true, V>) : resident(k_forward<TL, false, kVarF32>);
+      return cudaSuccess;
+    });
+    return n;
   }
 
   static const EngineOps* ops() {
     static const EngineOps o = {TL::N,         TL::G,      TL::T,       TL::R1,      TL::R2,
                                 TL::SMEM,      &probe_spectrum, &forward, &adjoint,  &probe_grad,
                                 &fft_debug,    &modesum,   &loss,       &seed,       &adjoint_fused,
-                                &resident_fused, &resident_clusters};
+                                &resident_fused, &resident_clusters, ALLV};
     return &o;
   }
 };

@@ -6,12 +6,57 @@
 // wavefield in shared memory across all slices.  Items of several problems
 // with the same window size may share one launch (serving).
 #pragma once
+#include <float.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "launch.h"
+#include "noise.cuh"
 #include "tile.cuh"
 
 namespace ptycho {
+
+// Entry-wave copies between the forward pass and the object-gradient term:
+// FP32, binary16 or bfloat16 per part (PREC 0 / 1 / 2), rounded to nearest
+// even on the way out, widened exactly on the way back.  The format is a
+// template parameter of the kernels, so the prefetched loads stay
+// branch-free.
+template <int PREC>
+__device__ __forceinline__ void wave_put(char* base, int i, float2 v) {
+  if constexpr (PREC == 0) {
+    reinterpret_cast<float2*>(base)[i] = v;
+  } else if constexpr (PREC == 1) {
+    reinterpret_cast<__half2*>(base)[i] = __floats2half2_rn(v.x, v.y);
+  } else {
+    reinterpret_cast<__nv_bfloat162*>(base)[i] = __floats2bfloat162_rn(v.x, v.y);
+  }
+}
+template <int PREC>
+__device__ __forceinline__ float2 wave_get(const char* base, int i) {
+  if constexpr (PREC == 0) {
+    return __ldcs(reinterpret_cast<const float2*>(base) + i);
+  } else {
+    const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(base) + i);
+    if constexpr (PREC == 1) {
+      __half2 h;
+      memcpy(&h, &u, sizeof(u));
+      return __half22float2(h);
+    } else {
+      // bfloat16: the high half of a binary32 (real part in the low 16 bits)
+      return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+    }
+  }
+}
+// Compile-time properties of a kernel variant (launch.h: Variant).
+template <int V>
+struct Var {
+  static constexpr int prec = V == kVarEpie ? 0 : V;  // entry-wave storage format
+  static constexpr bool epie = V == kVarEpie;         // ePIE normalisers (§3.3.1)
+  static constexpr size_t wave_bytes = prec ? 4 : 8;
+};
 
 __device__ __forceinline__ const ProblemDesc& find_desc(const LaunchArgs& L, int item) {
   int d = 0;
@@ -98,14 +143,15 @@ struct PreO {
 struct PsiO {
   float2 psi, o;
 };
+template <int PREC>
 struct PrePsiO {
-  const float2* psi;  // entry wave of the slice, natural order, row stride N
+  const char* psi;  // entry wave of the slice, natural order, row stride N, format PREC
   int N;
   const float2* O;
   int W;
   using type = PsiO;
   __device__ PsiO operator()(int r, int c) const {
-    return {__ldcs(psi + r * N + c), __ldg(O + (size_t)r * W + c)};
+    return {wave_get<PREC>(psi, r * N + c), __ldg(O + (size_t)r * W + c)};
   }
 };
 
@@ -130,14 +176,17 @@ struct PropOp {
 };
 
 // One full forward pass of item (j, k) from the shifted probe to the far
-// field.  The entry wave psi_s of every slice is written to `waves` (natural
-// order, NP per slice) when it is non-null.  On return the column layout
+// field.  WAVES: the entry wave psi_s of every slice is written to `waves`
+// (natural order, NP per slice, format Var<V>::prec); ePIE variants also
+// record max |psi_s|^2 per slice in D.wmax.  On return the column layout
 // holds F(phi_{S-1}) after its column s1 stage: the caller applies the last
 // column s2 (far field) with its own pointwise op.
-template <class TL>
+template <class TL, int V, bool WAVES>
 __device__ void forward_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D, const ItemGeo& g,
-                              float2* waves) {
+                              char* waves) {
   constexpr int N = TL::N;
+  constexpr int PREC = Var<V>::prec;
+  constexpr bool WMAX = Var<V>::epie;
   const float inv = 1.0f / (float)TL::NP;
   const float2* Ph = D.Phat + (size_t)g.k * TL::NP;
   const float2* rY = sm.rampY;
@@ -153,15 +202,22 @@ __device__ void forward_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
   for (int s = 0; s < D.S; ++s) {
     if (s + 1 < D.S) load_chirp<TL>(sm.chirp + (s & 1) * N, D.Hc + (size_t)s * N);
     const float2* Os = D.O + (size_t)s * D.H * D.W + (size_t)g.ny * D.W + g.nx;
-    float2* wv = waves ? waves + (size_t)s * TL::NP : nullptr;
+    char* wv = WAVES ? waves + (size_t)s * TL::NP * Var<V>::wave_bytes : nullptr;
     const int W = D.W;
     // row s1' (finishing psi_s) -> store psi_s -> transmit -> row s1
-    TL::template row_strided<true, true>(
-        sm.wave, sm.twS, rank, NoLoad{}, PreO{Os, W},
-        [&](int r, int c, float2& v, const float2& o) {
-          if (wv) wv[r * N + c] = v;
-          v = cmul(v, o);
-        });
+    float lm = 0.f;
+    TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, PreO{Os, W},
+                                         [&](int r, int c, float2& v, const float2& o) {
+                                           if constexpr (WAVES) wave_put<PREC>(wv, r * N + c, v);
+                                           if constexpr (WMAX) lm = fmaxf(lm, cabs2(v));
+                                           v = cmul(v, o);
+                                         });
+    if constexpr (WMAX) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+      // non-negative floats order like their bit patterns
+      if ((threadIdx.x & 31) == 0) atomicMax(D.wmax + ((size_t)g.j * D.K + g.k) * D.S + s, __float_as_uint(lm));
+    }
     __syncthreads();
     TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
     if (s + 1 < D.S) {
@@ -174,10 +230,12 @@ __device__ void forward_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
 }
 
 // Backward pass of item (j, k) from g_phi_{S-1} (row layout, pending row
-// s1') to the probe spectrum gradient.  psi_s are read from `waves`.
-template <class TL>
+// s1') to the probe spectrum gradient.  psi_s are read from `waves`
+// (format Var<V>::prec).  ePIE variants scale the object term by
+// 1 / max|psi_s|^2 and the incident-wave term by 1 / max|O_s|^2 (§3.3.1).
+template <class TL, int V>
 __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D, const ItemGeo& g,
-                              const float2* waves) {
+                              const char* waves) {
   constexpr int N = TL::N;
 #pragma unroll 1
   for (int s = D.S - 1; s >= 0; --s) {
@@ -185,15 +243,25 @@ __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
     const size_t ooff = (size_t)s * D.H * D.W + (size_t)g.ny * D.W + g.nx;
     const float2* Os = D.O + ooff;
     float2* gOs = D.gO + ooff;
-    const float2* wv = waves + (size_t)s * TL::NP;
+    const char* wv = waves + (size_t)s * TL::NP * Var<V>::wave_bytes;
     const int W = D.W;
     // row s1' (finishing g_phi_s) -> object gradient, g_psi_s = conj(O) g_phi -> row s1
-    TL::template row_strided<true, true>(
-        sm.wave, sm.twS, rank, NoLoad{}, PrePsiO{wv, N, Os, W},
-        [&](int r, int c, float2& v, const PsiO& p) {
-          red_add(gOs + (size_t)r * W + c, cconjmul(p.psi, v));
-          v = cconjmul(p.o, v);
-        });
+    if constexpr (Var<V>::epie) {
+      const float inv_o = 1.0f / fmaxf(__uint_as_float(__ldg(D.omax + s)), FLT_MIN);
+      const float inv_p =
+          1.0f / fmaxf(__uint_as_float(__ldcg(D.wmax + ((size_t)g.j * D.K + g.k) * D.S + s)), FLT_MIN);
+      TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, PrePsiO<Var<V>::prec>{wv, N, Os, W},
+                                           [&](int r, int c, float2& v, const PsiO& p) {
+                                             red_add(gOs + (size_t)r * W + c, cscale(cconjmul(p.psi, v), inv_p));
+                                             v = cscale(cconjmul(p.o, v), inv_o);
+                                           });
+    } else {
+      TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, PrePsiO<Var<V>::prec>{wv, N, Os, W},
+                                           [&](int r, int c, float2& v, const PsiO& p) {
+                                             red_add(gOs + (size_t)r * W + c, cconjmul(p.psi, v));
+                                             v = cconjmul(p.o, v);
+                                           });
+    }
     __syncthreads();
     TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
     if (s > 0) {
@@ -250,7 +318,7 @@ __device__ __forceinline__ int my_rank() {
 // ---------------------------------------------------------------------------
 // Forward: far field A = F(phi_{S-1}) (unnormalised, spectral slot order) of
 // every item; optionally every entry wave psi_s (STORE).
-template <class TL, bool STORE>
+template <class TL, bool STORE, int V>
 __global__ void __launch_bounds__(TL::T, TL::MINB) k_forward(const __grid_constant__ LaunchArgs L) {
   extern __shared__ float4 smem_raw[];
   Smem<TL> sm(smem_raw);
@@ -271,8 +339,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_forward(const __grid_consta
     __syncthreads();
     make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
     __syncthreads();
-    float2* waves = STORE ? D.waves + ((size_t)g.j * D.K + g.k) * D.S * TL::NP : nullptr;
-    forward_chain<TL>(sm, rank, D, g, waves);
+    char* waves = STORE ? D.waves + ((size_t)g.j * D.K + g.k) * D.S * TL::NP * Var<V>::wave_bytes : nullptr;
+    forward_chain<TL, V, STORE>(sm, rank, D, g, waves);
     float2* Aout = D.A + ((size_t)g.j * D.K + g.k) * TL::NP;
     TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{},
                                                [&](int pu, int pv, float2& v) { Aout[pu * N + pv] = v; });
@@ -283,7 +351,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_forward(const __grid_consta
 // w . A from global memory.  Otherwise the forward is recomputed here with
 // psi_s written to this cluster's slot, and the far field is turned into
 // the seed without leaving shared memory.
-template <class TL, bool STORE>
+template <class TL, bool STORE, int V>
 __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_constant__ LaunchArgs L) {
   extern __shared__ float4 smem_raw[];
   Smem<TL> sm(smem_raw);
@@ -305,42 +373,24 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_consta
     make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
     __syncthreads();
     const float* wj = D.w + (size_t)g.j * TL::NP;
-    const float2* waves;
+    const char* waves;
     if constexpr (STORE) {
-      waves = D.waves + ((size_t)g.j * D.K + g.k) * D.S * TL::NP;
+      waves = D.waves + ((size_t)g.j * D.K + g.k) * D.S * TL::NP * Var<V>::wave_bytes;
       const float2* Aj = D.A + ((size_t)g.j * D.K + g.k) * TL::NP;
       TL::template col_contig<false, false, true>(
           sm.wave, sm.twC, rank, [&](int pu, int pv) { return cscale(Aj[pu * N + pv], wj[pu * N + pv]); },
           NoOp{});
       __syncthreads();
     } else {
-      float2* slot = L.slots + (size_t)cluster_id<TL>() * L.slot_stride;
+      char* slot = L.slots + (size_t)cluster_id<TL>() * L.slot_stride;
       waves = slot;
-      forward_chain<TL>(sm, rank, D, g, slot);
+      forward_chain<TL, V, true>(sm, rank, D, g, slot);
       TL::template col_contig<true, true, true>(sm.wave, sm.twC, rank, NoLoad{},
                                                 [&](int pu, int pv, float2& v) { v = cscale(v, wj[pu * N + pv]); });
       __syncthreads();
     }
     TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
-    adjoint_chain<TL>(sm, rank, D, g, waves);
-  }
-}
-
-// Noise-model loss per pixel and its derivative dl/dI (float, the
-// cancellation-free forms of k_loss).
-__device__ __forceinline__ void noise_model(int model, float eps, float c, float I, float E, float& l, float& dl) {
-  if (model == 0) {
-    const float sa = sqrtf(I + c + eps), sb = sqrtf(E + c + eps);
-    const float diff = (I - E) / (sa + sb);
-    l = 0.5f * diff * diff;
-    dl = 0.5f * (1.0f - sb / sa);
-  } else if (model == 1) {
-    l = (I - E) - E * log1pf((I - E) / (E + eps));
-    dl = 1.0f - E / (I + eps);
-  } else {
-    const float r = (I - E) / (c * c);
-    l = 0.5f * r * (I - E);
-    dl = r;
+    adjoint_chain<TL, V>(sm, rank, D, g, waves);
   }
 }
 
@@ -361,7 +411,7 @@ constexpr unsigned long long kSpinLimit = 1ull << 22;  // x 128 ns sleeps: about
 // seed 2 l'(I) / NP from the mode sum, and runs the backward pass.  Mode 0
 // accumulates the position's loss.  A wait that runs out sets the status
 // word and continues (wrong gradients, no hang).
-template <class TL>
+template <class TL, int V>
 __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_fused(const __grid_constant__ LaunchArgs L,
                                                                    const __grid_constant__ FusedArgs F) {
   extern __shared__ float4 smem_raw[];
@@ -374,7 +424,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_fused(const __grid_
   const int cid = cluster_id<TL>();
   const int gi = cid / K, k = cid - gi * K;
   if (gi >= F.groups) return;  // the whole cluster leaves together
-  float2* slot = L.slots + (size_t)cid * L.slot_stride;
+  char* slot = L.slots + (size_t)cid * L.slot_stride;
   const unsigned need = (unsigned)(K * TL::G);
 #pragma unroll 1
   for (int round = 0;; ++round) {
@@ -389,7 +439,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_fused(const __grid_
     __syncthreads();
     make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
     __syncthreads();
-    forward_chain<TL>(sm, rank, D, g, slot);
+    forward_chain<TL, V, true>(sm, rank, D, g, slot);
     float* Ij = F.Ibuf + ((size_t)j * K + k) * TL::NP;
     TL::template col_contig<true, true, false, true>(
         sm.wave, sm.twC, rank, NoLoad{},
@@ -429,7 +479,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_fused(const __grid_
     }
     __syncthreads();
     TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
-    adjoint_chain<TL>(sm, rank, D, g, slot);
+    adjoint_chain<TL, V>(sm, rank, D, g, slot);
   }
 }
 

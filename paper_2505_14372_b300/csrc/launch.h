@@ -8,6 +8,12 @@ namespace ptycho {
 constexpr int kMaxDesc = 16;           // problems per batched launch
 constexpr unsigned PTYCHO_STATUS_OUT_OF_BOUNDS = 1u;
 constexpr unsigned PTYCHO_STATUS_TIMEOUT = 2u;     // a bounded device wait ran out
+constexpr int kModelEpie = 3;                      // noise-model id of the ePIE modulus update
+
+// Kernel variants of the forward / adjoint kernels: the storage format of
+// the entry-wave copies (FP32, binary16, bfloat16) and the ePIE normalisers
+// are compile-time properties of their real-space stages.
+enum Variant { kVarF32 = 0, kVarF16 = 1, kVarBF16 = 2, kVarEpie = 3 };
 
 // One problem (dataset) inside a launch.  All pointers are device pointers.
 struct ProblemDesc {
@@ -18,7 +24,7 @@ struct ProblemDesc {
   const float2* Hc;     // [S-1][N] separable Fresnel chirp per gap, slot order
   float2* A;            // [B][K][NP] far field F(phi), slot order
   const float* w;       // [B][NP] 2 l'(I) / NP, slot order (adjoint)
-  float2* waves;        // STORE: [B][K][S][NP] entry waves (natural order)
+  char* waves;          // STORE: [B][K][S][NP] entry waves (natural order, the variant's format)
   float2* gO;           // [S][H][W] object gradient (accumulated)
   float2* gPhat;        // [K][NP] probe spectrum gradient (accumulated)
   double* gpos;         // [B][2] scan-position gradient (accumulated), or null
@@ -26,6 +32,10 @@ struct ProblemDesc {
   int npos;             // rows of pos (and of the pattern array) idx may select
   int blT;              // band limit keeps f_u^2 + f_v^2 <= blT; < 0: off
   int item0;            // first global item of this problem
+  // ePIE (null for the gradient): max |O_s|^2 per slice [S] and max |psi_s|^2
+  // per item and slice [B][K][S], both as float bits (atomicMax)
+  const unsigned* omax;
+  unsigned* wmax;
 };
 
 struct LaunchArgs {
@@ -33,8 +43,8 @@ struct LaunchArgs {
   int nd;
   int total;                // items over all problems
   unsigned* status;         // device status word (PTYCHO_STATUS_*)
-  float2* slots;            // recompute scratch, one slot per cluster
-  long long slot_stride;    // float2 per slot
+  char* slots;              // recompute scratch, one slot per cluster
+  long long slot_stride;    // bytes per slot
 };
 
 // Extra arguments of the fused loss + adjoint kernel (entry waves

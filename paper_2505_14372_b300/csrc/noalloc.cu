@@ -158,7 +158,8 @@ extern "C" int ptycho_forward_static(const ptycho_geom* g, const ptycho_c64* O, 
     la.nd = 1;
     la.total = B * K;
     la.status = status;
-    e = ops->forward(la, std::min(B * K, ops->resident_clusters(false, false)), false, s);
+    e = ops->forward(la, std::min(B * K, ops->resident_clusters(false, false, ptycho::kVarF32)), false,
+                     ptycho::kVarF32, s);
   }
   if (e == cudaSuccess) e = ops->modesum(A, I_out, B, K, s);
   if (e != cudaSuccess) {

@@ -475,6 +475,9 @@ int ptycho_submit(ptycho_server* s, const ptycho_request* q, uint64_t* ticket) {
   if (q->n_pos < 1 || !q->pos || !q->I_exp || !q->P_init || q->iterations < 1 || q->batch < 1)
     return perr(PTYCHO_EINVAL, "bad request (positions, patterns, probe, iterations, batch)");
   if (q->grouping != 0 && q->grouping != 1) return perr(PTYCHO_EINVAL, "grouping must be 0 or 1");
+  if ((q->opt.reg_obj_tv != 0.f || q->opt.reg_obj_layers_tv != 0.f) && !(q->opt.reg_tv_eps > 0.f))
+    return perr(PTYCHO_EINVAL, "TV regularisers need reg_tv_eps > 0");
+  if (g.wave_prec != PTYCHO_PREC_F32) return perr(PTYCHO_EINVAL, "served requests keep FP32 entry waves");
   {
     // host-side validation of the rest of the geometry through a probe context is
     // not possible without allocating; check the fields the kernels rely on

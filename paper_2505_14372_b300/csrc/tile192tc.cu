@@ -112,22 +112,23 @@ cudaError_t ensure_tables(int R1, int R2) {
 template <int MODE>
 struct TcEngine {
   using TL = TileTC<Tile<192, 2, 16, 384, 1>, MODE>;
-  using E = Engine<TL>;
+  using E = Engine<TL, false>;  // FP32 entry waves and the gradient only
   static cudaError_t probe_spectrum(const float2* P, float2* Phat, int K, cudaStream_t s) {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
     return e != cudaSuccess ? e : E::probe_spectrum(P, Phat, K, s);
   }
-  static cudaError_t forward(const LaunchArgs& L, int clusters, bool store, cudaStream_t s) {
+  static cudaError_t forward(const LaunchArgs& L, int clusters, bool store, int variant, cudaStream_t s) {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
-    return e != cudaSuccess ? e : E::forward(L, clusters, store, s);
+    return e != cudaSuccess ? e : E::forward(L, clusters, store, variant, s);
   }
-  static cudaError_t adjoint(const LaunchArgs& L, int clusters, bool store, cudaStream_t s) {
+  static cudaError_t adjoint(const LaunchArgs& L, int clusters, bool store, int variant, cudaStream_t s) {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
-    return e != cudaSuccess ? e : E::adjoint(L, clusters, store, s);
+    return e != cudaSuccess ? e : E::adjoint(L, clusters, store, variant, s);
   }
-  static cudaError_t adjoint_fused(const LaunchArgs& L, const FusedArgs& F, int clusters, cudaStream_t s) {
+  static cudaError_t adjoint_fused(const LaunchArgs& L, const FusedArgs& F, int clusters, int variant,
+                                   cudaStream_t s) {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
-    return e != cudaSuccess ? e : E::adjoint_fused(L, F, clusters, s);
+    return e != cudaSuccess ? e : E::adjoint_fused(L, F, clusters, variant, s);
   }
   static cudaError_t probe_grad(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s) {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);

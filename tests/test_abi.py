@@ -96,3 +96,13 @@ def test_compact_groups_are_spatially_compact():
     def spread(order):
         return np.mean([np.ptp(pos[order[i:i + B]], axis=0).sum() for i in range(0, P, B)])
     assert spread(comp) < 0.5 * spread(sparse)
+
+
+def test_reduced_precision_halves_store_scratch():
+    # 16-bit entry-wave copies take half the bytes of complex64 ones
+    geom = Geometry(S=5, K=2, N=64, H=80, W=80, dz=(10.0,) * 4)
+    full = scratch_bytes(geom, 64, "store")
+    geom.wave_prec = "bf16"
+    half = scratch_bytes(geom, 64, "store")
+    waves = 64 * 2 * 5 * 64 * 64 * 8
+    assert full - half == pytest.approx(waves / 2, abs=512)

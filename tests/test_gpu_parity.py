@@ -172,16 +172,19 @@ def test_gaussian_noise_model_parity():
     assert rel_l2(host(gO), rO) < TOL_MS and rel_l2(host(gP), rP) < TOL_MS
 
 
-def test_step_with_regularizers_parity():
+@pytest.mark.parametrize("reg", [dict(l2_obj=0.05, tikhonov=0.05, layers=0.5, l2_probe=1e-3),
+                                 dict(tv=0.5, tv_layers=2.0, tv_eps=0.02, l2_probe=1e-3)])
+def test_step_with_regularizers_parity(reg):
     geom, og, P, O, pos = problem(73, 3, 2, 64, 90, 90, 10, loss="poisson", eps=0.8)
     I_exp = np.random.default_rng(6).poisson(orc.forward(O, P, pos, og) + 0.5).astype(np.float32)
-    reg = dict(l2_obj=0.05, tikhonov=0.05, layers=0.5, l2_probe=1e-3)
     idx = np.array([1, 4, 7, 9, 0], np.int32)
     ctx = Context(geom, max_batch=5)
     Od, Pd = dev(O), dev(P)
     st = AdamState(geom)
-    opt = adam_opt(lr_O=1e-2, lr_P=1e-3, reg_obj_l2=reg["l2_obj"], reg_obj_tikhonov=reg["tikhonov"],
-                   reg_obj_layers=reg["layers"], reg_probe_l2=reg["l2_probe"])
+    opt = adam_opt(lr_O=1e-2, lr_P=1e-3, reg_obj_l2=reg.get("l2_obj", 0.0), reg_obj_tikhonov=reg.get("tikhonov", 0.0),
+                   reg_obj_layers=reg.get("layers", 0.0), reg_probe_l2=reg.get("l2_probe", 0.0),
+                   reg_obj_tv=reg.get("tv", 0.0), reg_obj_layers_tv=reg.get("tv_layers", 0.0),
+                   reg_tv_eps=reg.get("tv_eps", 1e-3))
     stats = host(ctx.step(Od, Pd, st, opt, dev(pos), dev(I_exp), dev(idx)))
     z = np.zeros
     O2, P2, *_, L, gn = orc.step(O, P, z(O.shape, complex), z(O.shape), z(P.shape, complex), z(P.shape), 1, pos,

@@ -375,7 +375,9 @@ def test_gaussian_model_and_fd():
 
 
 @pytest.mark.parametrize("kw", [dict(l2_obj=0.3), dict(l2_probe=0.2), dict(tikhonov=0.4), dict(layers=0.5),
-                                dict(l2_obj=0.1, tikhonov=0.2, layers=0.3, l2_probe=0.05)])
+                                dict(l2_obj=0.1, tikhonov=0.2, layers=0.3, l2_probe=0.05),
+                                dict(tv=0.3, tv_eps=0.05), dict(tv_layers=0.4, tv_eps=0.02),
+                                dict(tv=0.2, tv_layers=0.1, tikhonov=0.1, tv_eps=0.1)])
 def test_regularizer_gradients_by_fd(kw):
     O = crand(3, 5, 6)
     P = crand(2, 4, 4)
@@ -399,3 +401,20 @@ def test_regularizers_vanish_on_their_null_space():
     P = crand(1, 4, 4)
     assert orc.regularizers(O, P, tikhonov=1.0, layers=1.0)[0] < 1e-24
     assert orc.regularizers(np.ones((2, 3, 3), complex), P, l2_obj=1.0)[0] == 0.0
+    assert orc.regularizers(O, P, tv=1.0, tv_layers=1.0, tv_eps=1e-3)[0] == 0.0
+
+
+def test_tv_of_a_phase_step_is_closed_form():
+    # one slice, O = 1 on the left half and exp(i phi) on the right: only the
+    # H horizontal differences across the step are non-zero, each of modulus
+    # |exp(i phi) - 1| = 2 sin(phi / 2)
+    H, W, phi, lam, eta = 6, 8, 0.7, 0.25, 1e-3
+    O = np.ones((1, H, W), complex)
+    O[:, :, W // 2:] = np.exp(1j * phi)
+    val, gO, _ = orc.regularizers(O, np.zeros((1, 2, 2), complex), tv=lam, tv_eps=eta)
+    d = 2 * np.sin(phi / 2)
+    assert np.isclose(val, lam * H * (np.sqrt(d * d + eta * eta) - eta), rtol=1e-12)
+    # the gradient pulls the two sides of the step towards each other
+    unit = (np.exp(1j * phi) - 1) / abs(np.exp(1j * phi) - 1)
+    assert np.allclose(gO[0, :, W // 2], lam * unit * d / np.sqrt(d * d + eta * eta))
+    assert np.allclose(gO[0, :, W // 2 - 1], -lam * unit * d / np.sqrt(d * d + eta * eta))
