@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--rate", type=float, default=16.0, help="mean request arrivals per second")
     ap.add_argument("--precision", action="store_true",
                     help="relative L2 error of every DFT mode against the FP64 oracle on a 4-position sub-problem")
+    ap.add_argument("--engine", default="gd", choices=["gd", "epie"],
+                    help="gd: gradient descent with Adam (ptycho_step); epie: the ePIE / 3PIE update "
+                         "(ptycho_epie_step, amplitude noise model)")
+    ap.add_argument("--positions", type=int, default=0,
+                    help="use only the first P scan positions (small profiling cases; the line says so)")
     ap.add_argument("--group", type=int, default=0,
                     help="override the group size (small cases for profiling; not a bench line)")
     return ap.parse_args()
@@ -142,7 +147,7 @@ def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_14372_b300", "csrc")
-    for name in ("radix.cuh", "tile.cuh", "kernels.cuh", "elementwise.cuh"):
+    for name in ("radix.cuh", "tile.cuh", "kernels.cuh", "elementwise.cuh", "noise.cuh", "launch.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -385,7 +390,13 @@ def main():
     if args.group:
         import dataclasses
         wl = dataclasses.replace(wl, B=args.group)
+    if args.positions:  # fewer raster rows, same object and window
+        import dataclasses
+        nx = wl.scan[1]
+        wl = dataclasses.replace(wl, scan=(max(1, min(args.positions, wl.P) // nx), nx))
     geom = workload_geometry(wl, args.waves, args.dft, args.wave_prec)
+    if args.engine == "epie":  # ePIE's modulus update belongs to the amplitude model
+        geom.loss, geom.eps, geom.c = "amplitude", 1e-3, 0.0
     B = wl.B
 
     # ---- inputs resident in HBM
@@ -410,8 +421,14 @@ def main():
     def group(i):
         return idx_all[i * B:(i + 1) * B]
 
+    def one_step(i):
+        if args.engine == "epie":
+            ctx.epie_step(Od, Pd, pos_d, Iexp_d, group(i), beta_O=0.5, beta_P=0.5, loss=stats[:1])
+        else:
+            ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, group(i), stats=stats)
+
     for i in range(args.warmup):
-        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, group(i), stats=stats)
+        one_step(i)
     torch.cuda.synchronize()
     ctx.check_status()
     if world > 1:
@@ -425,7 +442,7 @@ def main():
     torch.cuda.synchronize()
     e0.record()
     for i in range(args.steps):
-        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, group(args.warmup + i), stats=stats)
+        one_step(args.warmup + i)
     e1.record()
     torch.cuda.synchronize()
     launches = kernels_launched() - k0
@@ -453,16 +470,30 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    if args.engine == "epie":
+        # the public ePIE call takes device arrays: the timed region copies
+        # each group's positions and patterns in and reads its loss back
+        pos_g = torch.empty((B, 2), dtype=torch.float32, device=dev)
+        I_g = torch.empty((B, wl.N, wl.N), dtype=torch.float32, device=dev)
+        ident = torch.arange(B, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        ctx.step_host(Od, Pd, st, opt, pos_host[i * B:(i + 1) * B], I_host[i * B:(i + 1) * B])
+        if args.engine == "epie":
+            pos_g.copy_(pos_host[i * B:(i + 1) * B], non_blocking=True)
+            I_g.copy_(I_host[i * B:(i + 1) * B], non_blocking=True)
+            float(ctx.epie_step(Od, Pd, pos_g, I_g, ident, beta_O=0.5, beta_P=0.5).item())
+        else:
+            ctx.step_host(Od, Pd, st, opt, pos_host[i * B:(i + 1) * B], I_host[i * B:(i + 1) * B])
     t_e2e = time.perf_counter() - t0
     te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e = {"value": world * B * e2e_steps / float(te.item()), "unit": "positions/s",
-           "h2d_bytes_per_step": B * 2 * 4 + B * wl.N * wl.N * 4, "d2h_bytes_per_step": 16,
-           "api": "ptycho_step_host (pinned host buffers)"}
+           "h2d_bytes_per_step": B * 2 * 4 + B * wl.N * wl.N * 4,
+           "d2h_bytes_per_step": 8 if args.engine == "epie" else 16,
+           "api": ("ptycho_epie_step after pinned host-to-device copies" if args.engine == "epie"
+                   else "ptycho_step_host (pinned host buffers)")}
 
     # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
     dom = max(ktimes, key=lambda k: ktimes[k][0])
@@ -497,7 +528,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "positions/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_dict(wl, args.waves, args.dft, args.wave_prec), "roofline": roofline, "e2e": e2e,
+                "config": dict(config_dict(wl, args.waves, args.dft, args.wave_prec), engine=args.engine,
+                               **({"loss": "amplitude"} if args.engine == "epie" else {}),
+                               **({"positions_used": wl.P} if args.positions else {})),
+                "roofline": roofline, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "last_stats": loss_last}
         if world == 1 and not args.no_baseline:
             n_s = 8 if wl.S > 1 else 64

@@ -72,9 +72,11 @@ typedef void* ptycho_stream;
 typedef enum { PTYCHO_LOSS_AMPLITUDE = 0, PTYCHO_LOSS_POISSON = 1, PTYCHO_LOSS_GAUSSIAN = 2 } ptycho_loss;
 
 /* How the adjoint gets the entry wave of every slice: STORE keeps all of
- * them from the forward pass (B*K*S*N*N*8 bytes of scratch), RECOMPUTE
- * re-runs the forward inside the adjoint kernel into per-cluster scratch,
- * AUTO stores when it fits the scratch budget. */
+ * them from the forward pass (B*K*S*N*N*8 bytes of scratch); RECOMPUTE runs
+ * the forward pass inside the adjoint kernel, one cluster per scan position
+ * at a time, so only min(B, resident clusters) positions' entry waves
+ * (K*S*N*N*8 bytes each) exist at once; AUTO stores when it fits the
+ * scratch budget.  (Halve the wave bytes for 16-bit storage.) */
 typedef enum { PTYCHO_WAVES_AUTO = 0, PTYCHO_WAVES_STORE = 1, PTYCHO_WAVES_RECOMPUTE = 2 } ptycho_waves;
 
 /* Evaluation of the small DFTs inside the shared-memory FFT tile: radix

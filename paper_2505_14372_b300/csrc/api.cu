@@ -24,7 +24,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Offsets of one call's scratch inside the context arena.
 struct Layout {
-  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, cnt, omax, wmax, waves, total;
+  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, omax, wmax, waves, pA, pI, total;
 };
 
 Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
@@ -41,16 +41,19 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   L.w = take((size_t)B * NP * 4);
   L.gPhat = take((size_t)g.K * NP * 8);
   // loss partials: block sums of the loss kernel, or one per position for
-  // the fused kernel; then regulariser and gradient-norm partials
+  // the position-major kernel; then regulariser and gradient-norm partials
   L.partials = take((size_t)(std::max(ptycho::kLossBlocks, B) + 3 * ptycho::kNormBlocks + 8) * 8);
   L.stats = take(4 * 8);
   L.stage_pos = take((size_t)B * 2 * 4);
   L.stage_I = take((size_t)B * NP * 4);
-  L.cnt = take((size_t)B * 4);
   L.omax = take((size_t)g.S * 4);
   L.wmax = take((size_t)B * g.K * g.S * 4);
   const size_t esize = g.wave_prec ? 4 : 8;  // entry-wave copies: complex64 or two 16-bit parts
-  L.waves = take(store ? (size_t)B * g.K * g.S * NP * esize : (size_t)slots * g.S * NP * esize);
+  // stored: every item's entry waves; recomputed: per cluster the entry waves
+  // of all K modes of its position, their far fields and the intensity
+  L.waves = take(store ? (size_t)B * g.K * g.S * NP * esize : (size_t)slots * g.K * g.S * NP * esize);
+  L.pA = take(store ? 0 : (size_t)slots * g.K * NP * 8);
+  L.pI = take(store ? 0 : (size_t)slots * NP * 4);
   L.total = off;
   return L;
 }
@@ -114,9 +117,8 @@ struct ptycho_ctx {
   size_t arena_bytes = 0;
   bool store = true;
   int slots = 0;          // recompute slots (clusters of the recompute adjoint)
-  int fused_clusters = 0; // resident clusters of the fused loss + adjoint kernel
-  int fused_epie = 0;     // the same for its ePIE variant
-  int res_fwd = 1, res_adj = 1;
+  int pos_clusters = 0;   // clusters of the position-major loss + adjoint (<= slots)
+  int res_fwd = 1, res_adj = 1, res_rec = 1;
   // timing
   bool timing = false;
   struct Pending {
@@ -265,41 +267,30 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
     Timed t(c, "slice_max", s);
     CK(ptycho::launch_slice_absmax(reinterpret_cast<const float2*>(O), c->g.S, (long long)c->g.H * c->g.W, omax, s));
   }
-  // Entry waves recomputed: one fused loss + adjoint launch when all mode
-  // clusters of a round fit on the device at once (cooperative launch).
+  // Entry waves recomputed: one position-major loss + adjoint launch (each
+  // cluster takes whole scan positions, all modes in turn).
   const int variant = epie ? ptycho::kVarEpie : c->g.wave_prec;
-  const int fused = epie ? c->fused_epie : c->fused_clusters;
-  if (!c->store && !vjp && fused >= K) {
-    if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
-    ptycho::FusedArgs F{};
+  if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
+  if (!c->store && !vjp && c->pos_clusters > 0) {
+    ptycho::PosArgs F{};
     F.Iexp = Iexp;
-    F.Ibuf = reinterpret_cast<float*>(c->arena + L.A);
-    F.cnt = reinterpret_cast<unsigned*>(c->arena + L.cnt);
+    F.Abuf = reinterpret_cast<float2*>(c->arena + L.pA);
+    F.Ibuf = reinterpret_cast<float*>(c->arena + L.pI);
     F.lpart = partials;
     F.model = model;
     F.eps = (float)c->g.eps;
     F.c = (float)c->g.c;
-    F.groups = fused / K;
-    CK(cudaMemsetAsync(F.cnt, 0, (size_t)B * 4, s));
     CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
     LaunchArgs la = one_problem(c, L, d);
-    cudaError_t e;
+    la.slot_stride = (long long)K * c->g.S * c->NP * (c->g.wave_prec ? 4 : 8);
     {
       Timed t(c, "adjoint", s);
-      e = c->ops->adjoint_fused(la, F, F.groups * K, variant, s);
+      CK(c->ops->adjoint_pos(la, F, std::min(B, c->pos_clusters), variant, s));
     }
-    if (e == cudaSuccess) {
-      *nl_out = B;
-      Timed t(c, "probe_grad", s);
-      CK(c->ops->probe_grad(gPhat, reinterpret_cast<float2*>(gP), K, accumulate, s));
-      return PTYCHO_OK;
-    }
-    // the device refused the cooperative launch: take the two-kernel path
-    cudaGetLastError();
-    if (epie) c->fused_epie = 0;
-    else c->fused_clusters = 0;
-  } else if (gpos && !accumulate) {
-    CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
+    *nl_out = B;
+    Timed t(c, "probe_grad", s);
+    CK(c->ops->probe_grad(gPhat, reinterpret_cast<float2*>(gP), K, accumulate, s));
+    return PTYCHO_OK;
   }
   LaunchArgs la = one_problem(c, L, d);
   const int items = B * K;
@@ -317,7 +308,9 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   }
   {
     Timed t(c, "adjoint", s);
-    const int cl = c->store ? std::min(items, c->res_adj) : std::min(items, c->slots);
+    // recomputing two-kernel path: one item per slot of S entry waves (the
+    // region holds K of them per position slot)
+    const int cl = c->store ? std::min(items, c->res_adj) : std::min({items, c->res_rec, c->slots * K});
     CK(c->ops->adjoint(la, cl, c->store, variant, s));
   }
   {
@@ -360,10 +353,12 @@ static int create_impl(const ptycho_geom* geom, int32_t max_batch, size_t scratc
   }
   const int var = geom->wave_prec;  // kVarF32 / kVarF16 / kVarBF16
   c->res_fwd = c->ops->resident_clusters(false, false, ptycho::kVarF32);
-  c->slots = c->ops->resident_clusters(true, false, var);
+  c->res_rec = c->ops->resident_clusters(true, false, var);
   c->res_adj = c->ops->resident_clusters(true, true, var);
-  c->fused_clusters = std::min(c->slots, c->ops->resident_fused(var));
-  c->fused_epie = c->ops->has_variants ? std::min(c->slots, c->ops->resident_fused(ptycho::kVarEpie)) : 0;
+  // position slots: no more clusters than can run at once or than positions
+  // in a call
+  c->slots = std::max(1, std::min(c->res_rec, max_batch));
+  c->pos_clusters = external_slots ? 0 : c->slots;
   // waves mode
   const Layout Ls = make_layout(c->g, max_batch, true, 0);
   const Layout Lr = make_layout(c->g, max_batch, false, external_slots ? 0 : c->slots);
@@ -440,6 +435,7 @@ size_t ptycho_scratch_bytes(const ptycho_geom* geom, int32_t B, int32_t waves) {
   int dev;
   if (cudaGetDevice(&dev) == cudaSuccess) slots = ops->resident_clusters(true, false, geom->wave_prec);
   else cudaGetLastError();
+  slots = std::max(1, std::min(slots, B));
   return make_layout(*geom, B, waves != PTYCHO_WAVES_RECOMPUTE, slots).total;
 }
 
@@ -646,8 +642,6 @@ int ptycho_check(ptycho_ctx* c, ptycho_stream stream) {
   unsigned st = 0;
   CK(cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
   CK(cudaMemset(c->status, 0, sizeof(unsigned)));
-  if (st & ptycho::PTYCHO_STATUS_TIMEOUT)
-    return perr(PTYCHO_ETIMEDOUT, "a bounded device wait ran out; the last gradients are not valid");
   if (st & ptycho::PTYCHO_STATUS_OUT_OF_BOUNDS)
     return perr(PTYCHO_EOUTOFBOUNDS, "a scan window left the object; its item was skipped");
   return PTYCHO_OK;

@@ -20,11 +20,11 @@ struct EngineOps {
   cudaError_t (*loss)(const float2* A, const float* Iexp, const int* idx, int npos, int B, int K, int model,
                       float eps, float c, float* w, double* partials, int nblocks, cudaStream_t s);
   cudaError_t (*seed)(const float* gI, int B, float* w, cudaStream_t s);
-  // fused loss + adjoint (cooperative cluster launch of `clusters` clusters)
-  cudaError_t (*adjoint_fused)(const LaunchArgs& L, const FusedArgs& F, int clusters, int variant, cudaStream_t s);
-  int (*resident_fused)(int variant);
   // resident clusters of the forward / adjoint kernels on the current device
   int (*resident_clusters)(bool adjoint, bool store, int variant);
+  // position-major loss + adjoint (entry waves recomputed; `clusters` clusters)
+  cudaError_t (*adjoint_pos)(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s);
+  int (*resident_pos)(int variant);
   bool has_variants;  // reduced-precision waves and ePIE are instantiated
 };
 

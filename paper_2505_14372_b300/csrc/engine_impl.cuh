@@ -49,34 +49,6 @@ struct Engine {
     return cudaLaunchKernelEx(&cfg, kernel, args...);
   }
 
-  // cooperative cluster launch: all clusters resident at once or an error
-  template <class K>
-  static cudaError_t launch_coop(K kernel, int clusters, cudaStream_t s, auto... args) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(clusters * TL::G), 1, 1);
-    cfg.blockDim = dim3(TL::T, 1, 1);
-    cfg.dynamicSmemBytes = TL::SMEM;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[2];
-    int n = 0;
-    attr[n].id = cudaLaunchAttributeCooperative;
-    attr[n].val.cooperative = 1;
-    ++n;
-    if (TL::G > 1) {
-      attr[n].id = cudaLaunchAttributeClusterDimension;
-      attr[n].val.clusterDim.x = TL::G;
-      attr[n].val.clusterDim.y = 1;
-      attr[n].val.clusterDim.z = 1;
-      ++n;
-    }
-    cfg.attrs = attr;
-    cfg.numAttrs = n;
-    count_launch();
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-  }
-
   template <class K>
   static int resident(K kernel) {
     int dev = 0, nsm = 0;
@@ -155,15 +127,14 @@ struct Engine {
     k_seed<TL><<<blocks, 256, 0, s>>>(gI, B, w);
     return cudaGetLastError();
   }
-  static cudaError_t adjoint_fused(const LaunchArgs& L, const FusedArgs& F, int clusters, int variant,
-                                   cudaStream_t s) {
+  static cudaError_t adjoint_pos(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s) {
     return with_variant(variant,
-                        [&](auto v) { return launch_coop(k_adjoint_fused<TL, decltype(v)::value>, clusters, s, L, F); });
+                        [&](auto v) { return launch(k_adjoint_pos<TL, decltype(v)::value>, clusters, s, L, F); });
   }
-  static int resident_fused(int variant) {
+  static int resident_pos(int variant) {
     int n = 0;
     with_variant(variant, [&](auto v) {
-      n = resident(k_adjoint_fused<TL, decltype(v)::value>);
+      n = resident(k_adjoint_pos<TL, decltype(v)::value>);
       return cudaSuccess;
     });
     return n;
@@ -182,8 +153,8 @@ struct Engine {
   static const EngineOps* ops() {
     static const EngineOps o = {TL::N,         TL::G,      TL::T,       TL::R1,      TL::R2,
                                 TL::SMEM,      &probe_spectrum, &forward, &adjoint,  &probe_grad,
-                                &fft_debug,    &modesum,   &loss,       &seed,       &adjoint_fused,
-                                &resident_fused, &resident_clusters, ALLV};
+                                &fft_debug,    &modesum,   &loss,       &seed,       &resident_clusters,
+                                &adjoint_pos,  &resident_pos, ALLV};
     return &o;
   }
 };

@@ -394,92 +394,88 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_consta
   }
 }
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-constexpr unsigned long long kSpinLimit = 1ull << 22;  // x 128 ns sleeps: about half a second
-
-// Fused loss + adjoint with the entry waves recomputed (one launch per
-// step).  Cluster c handles mode k = c % K of position j = round * groups +
-// c / K, so the K clusters of one position run in the same round; a
-// cooperative launch keeps them all resident.  Each recomputes its forward
-// pass (entry waves to its slot), publishes |F phi|^2 of its mode, waits
-// (bounded) until all K modes of the position are published, forms the
-// seed 2 l'(I) / NP from the mode sum, and runs the backward pass.  Mode 0
-// accumulates the position's loss.  A wait that runs out sets the status
-// word and continues (wrong gradients, no hang).
+// Loss + adjoint with the entry waves recomputed, one cluster per scan
+// position (position-major, one launch per step, no waits between
+// clusters).  For position j the cluster runs the forward pass of every mode
+// k (entry waves to part k of its slot, far field A_k to its scratch, the
+// intensity summed over modes in its scratch), applies the noise model to
+// the mode sum (loss into lpart[j], seed weight 2 l'(I) / NP in place of I),
+// then runs the backward pass of every mode from the seed w A_k.  Every
+// pixel of the scratch is written and read back by the same thread (the
+// column stage's task mapping), so the scratch needs no synchronisation
+// beyond program order.
 template <class TL, int V>
-__global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_fused(const __grid_constant__ LaunchArgs L,
-                                                                   const __grid_constant__ FusedArgs F) {
+__global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_constant__ LaunchArgs L,
+                                                                 const __grid_constant__ PosArgs F) {
   extern __shared__ float4 smem_raw[];
   Smem<TL> sm(smem_raw);
   const int rank = my_rank<TL>();
   TL::init_tables(sm.twS, sm.twC, sm.fsq);
   constexpr int N = TL::N;
+  constexpr float inv = 1.0f / (float)TL::NP;
   const ProblemDesc& D = L.d[0];
   const int K = D.K;
   const int cid = cluster_id<TL>();
-  const int gi = cid / K, k = cid - gi * K;
-  if (gi >= F.groups) return;  // the whole cluster leaves together
   char* slot = L.slots + (size_t)cid * L.slot_stride;
-  const unsigned need = (unsigned)(K * TL::G);
+  const size_t wstride = (size_t)D.S * TL::NP * Var<V>::wave_bytes;  // one mode's entry waves
+  float2* Ab = F.Abuf + (size_t)cid * K * TL::NP;
+  float* Ib = F.Ibuf + (size_t)cid * TL::NP;
 #pragma unroll 1
-  for (int round = 0;; ++round) {
-    const int j = round * F.groups + gi;
-    if (j >= D.B) break;
+  for (int j = cid; j < D.B; j += n_clusters<TL>()) {
+    ItemGeo g = item_geo<TL>(D, j * K);
     TL::sync_cluster();
-    const ItemGeo g = item_geo<TL>(D, j * K + k);
     if (!g.ok) {  // every mode of this position skips it
       if (threadIdx.x == 0 && rank == 0) atomicOr(L.status, PTYCHO_STATUS_OUT_OF_BOUNDS);
       continue;
     }
-    __syncthreads();
     make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
     __syncthreads();
-    forward_chain<TL, V, true>(sm, rank, D, g, slot);
-    float* Ij = F.Ibuf + ((size_t)j * K + k) * TL::NP;
-    TL::template col_contig<true, true, false, true>(
-        sm.wave, sm.twC, rank, NoLoad{},
-        [&](int pu, int pv, float2& v) { Ij[pu * N + pv] = cabs2(v) * (1.0f / (float)TL::NP); });
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(F.cnt + j, 1u);
-      unsigned long long it = 0;
-      while (ld_acquire_gpu(F.cnt + j) < need) {
-        // give up after the limit, or at once when another wait already did
-        if (++it > kSpinLimit || (ld_acquire_gpu(L.status) & PTYCHO_STATUS_TIMEOUT)) {
-          atomicOr(L.status, PTYCHO_STATUS_TIMEOUT);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-    __syncthreads();
-    const float* Ibase = F.Ibuf + (size_t)j * K * TL::NP;
     const float* E = F.Iexp + (size_t)g.jj * TL::NP;
     float lsum = 0.f;
-    TL::template col_contig<true, false, true>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
-      const int p = pu * N + pv;
-      float I = 0.f;
-      for (int m = 0; m < K; ++m) I += __ldcg(Ibase + (size_t)m * TL::NP + p);
-      float l, dl;
-      noise_model(F.model, F.eps, F.c, I, __ldg(E + TL::nat(pu) * N + TL::nat(pv)), l, dl);
-      lsum += l;
-      v = cscale(v, 2.0f * dl * (1.0f / (float)TL::NP));
-    });
-    if (k == 0) {
-      double s = lsum;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if ((threadIdx.x & 31) == 0) atomicAdd(F.lpart + j, s);
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+      if (k) TL::sync_cluster();
+      g.k = k;
+      forward_chain<TL, V, true>(sm, rank, D, g, slot + k * wstride);
+      float2* Ak = Ab + (size_t)k * TL::NP;
+      const bool first = k == 0, last = k + 1 == K;
+      TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
+        const int p = pu * N + pv;
+        Ak[p] = v;
+        float I = cabs2(v) * inv;
+        if (!first) I += Ib[p];
+        if (!last) {
+          Ib[p] = I;
+        } else {
+          float l, dl;
+          noise_model(F.model, F.eps, F.c, I, __ldg(E + TL::nat(pu) * N + TL::nat(pv)), l, dl);
+          lsum += l;
+          Ib[p] = 2.0f * dl * inv;
+        }
+      });
     }
-    __syncthreads();
-    TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
-    adjoint_chain<TL, V>(sm, rank, D, g, slot);
+    {
+      double sd = lsum;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(F.lpart + j, sd);
+    }
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+      TL::sync_cluster();
+      g.k = k;
+      const float2* Ak = Ab + (size_t)k * TL::NP;
+      TL::template col_contig<false, false, true>(
+          sm.wave, sm.twC, rank,
+          [&](int pu, int pv) {
+            const int p = pu * N + pv;
+            return cscale(Ak[p], Ib[p]);
+          },
+          NoOp{});
+      __syncthreads();
+      TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+      adjoint_chain<TL, V>(sm, rank, D, g, slot + k * wstride);
+    }
   }
 }
 

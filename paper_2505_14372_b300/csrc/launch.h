@@ -7,7 +7,6 @@ namespace ptycho {
 
 constexpr int kMaxDesc = 16;           // problems per batched launch
 constexpr unsigned PTYCHO_STATUS_OUT_OF_BOUNDS = 1u;
-constexpr unsigned PTYCHO_STATUS_TIMEOUT = 2u;     // a bounded device wait ran out
 constexpr int kModelEpie = 3;                      // noise-model id of the ePIE modulus update
 
 // Kernel variants of the forward / adjoint kernels: the storage format of
@@ -47,16 +46,17 @@ struct LaunchArgs {
   long long slot_stride;    // bytes per slot
 };
 
-// Extra arguments of the fused loss + adjoint kernel (entry waves
-// recomputed; the K mode clusters of a position meet once per position).
-struct FusedArgs {
+// Extra arguments of the position-major loss + adjoint kernel: one cluster
+// per scan position runs the forward pass of every mode, the noise model on
+// the mode sum, then the backward pass of every mode.  Per-cluster scratch:
+// far fields and intensity / seed weights (and K entry-wave sets in the slot).
+struct PosArgs {
   const float* Iexp;   // [npos][NP] measured patterns, natural order
-  float* Ibuf;         // [B][K][NP] per-mode far-field intensity, slot order
-  unsigned* cnt;       // [B] CTAs that published their intensity (zeroed per launch)
+  float2* Abuf;        // [clusters][K][NP] far fields F(phi), slot order
+  float* Ibuf;         // [clusters][NP] mode-summed intensity, then 2 l'(I) / NP
   double* lpart;       // [B] loss per position (zeroed per launch)
   int model;           // noise model
   float eps, c;
-  int groups;          // positions per round = clusters / K
 };
 
 }  // namespace ptycho

@@ -125,10 +125,9 @@ struct TcEngine {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
     return e != cudaSuccess ? e : E::adjoint(L, clusters, store, variant, s);
   }
-  static cudaError_t adjoint_fused(const LaunchArgs& L, const FusedArgs& F, int clusters, int variant,
-                                   cudaStream_t s) {
+  static cudaError_t adjoint_pos(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s) {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
-    return e != cudaSuccess ? e : E::adjoint_fused(L, F, clusters, variant, s);
+    return e != cudaSuccess ? e : E::adjoint_pos(L, F, clusters, variant, s);
   }
   static cudaError_t probe_grad(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s) {
     cudaError_t e = ensure_tables(TL::R1, TL::R2);
@@ -145,7 +144,7 @@ struct TcEngine {
       x.forward = &forward;
       x.adjoint = &adjoint;
       x.probe_grad = &probe_grad;
-      x.adjoint_fused = &adjoint_fused;
+      x.adjoint_pos = &adjoint_pos;
       x.fft_debug = &fft_debug;
       return x;
     }();

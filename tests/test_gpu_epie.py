@@ -2,7 +2,7 @@
 against the FP64 oracle: the object and probe updates (new minus old),
 element by element, for single- and multi-slice, mixed-state problems, with
 stored and recomputed entry waves (the recompute path at 192x192 runs the
-fused cluster kernel).  Tolerance: relative L2 <= 1e-4, the gradient's
+position-major loss + adjoint kernel).  Tolerance: relative L2 <= 1e-4, the gradient's
 (the update is the adjoint chain with per-slice scalar normalisers)."""
 import numpy as np
 import pytest
