@@ -147,7 +147,8 @@ def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_14372_b300", "csrc")
-    for name in ("radix.cuh", "tile.cuh", "kernels.cuh", "elementwise.cuh", "noise.cuh", "launch.h"):
+    for name in ("radix.cuh", "tile.cuh", "kernels.cuh", "elementwise.cuh", "noise.cuh", "launch.h",
+                 "engine_impl.cuh", "tile64.cu", "tile128.cu", "tile192.cu", "tile256.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -356,6 +357,18 @@ def run_precision(args):
         ctx.check_status()
         out[mode] = {"I": rel(I, rI), "loss": abs(float(loss.item()) - L) / abs(L),
                      "gO": rel(gO.cpu().numpy(), rO), "gP": rel(gP.cpu().numpy(), rP)}
+        ctx.close()
+    # 16-bit entry-wave storage (FFT tile): errors against the unrounded
+    # oracle (the accuracy given up) and the oracle rounding the same copies
+    for prec in ("f16", "bf16"):
+        geom = workload_geometry(small, args.waves, "fft", prec)
+        ctx = Context(geom, max_batch=4)
+        loss, gO, gP = ctx.adjoint(d(O), d(P), d(pos), d(E))
+        ctx.check_status()
+        _, rOr, _ = orc.gradient(O, P, pos, E, og, wave_fmt=prec)
+        out["fft, " + prec + " entry waves"] = {"loss": abs(float(loss.item()) - L) / abs(L),
+                                                "gO": rel(gO.cpu().numpy(), rO), "gP": rel(gP.cpu().numpy(), rP),
+                                                "gO_vs_rounding_oracle": rel(gO.cpu().numpy(), rOr)}
         ctx.close()
     print(json.dumps({"mode": "precision", "metric": "relative L2 error against the FP64 oracle",
                       "config": {"workload": wl.name, "positions": "4 neighbouring raster positions",
