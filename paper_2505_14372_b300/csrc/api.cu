@@ -642,6 +642,8 @@ int ptycho_check(ptycho_ctx* c, ptycho_stream stream) {
   unsigned st = 0;
   CK(cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
   CK(cudaMemset(c->status, 0, sizeof(unsigned)));
+  if (c->ops->take_exchange_timeouts())
+    return perr(PTYCHO_ETIMEDOUT, "a bounded wait of the cluster exchange ran out; the last results are not valid");
   if (st & ptycho::PTYCHO_STATUS_OUT_OF_BOUNDS)
     return perr(PTYCHO_EOUTOFBOUNDS, "a scan window left the object; its item was skipped");
   return PTYCHO_OK;

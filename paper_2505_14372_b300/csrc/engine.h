@@ -25,6 +25,9 @@ struct EngineOps {
   // position-major loss + adjoint (entry waves recomputed; `clusters` clusters)
   cudaError_t (*adjoint_pos)(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s);
   int (*resident_pos)(int variant);
+  // bounded exchange waits of this tile's kernels that gave up since the
+  // last call (read and cleared)
+  unsigned (*take_exchange_timeouts)();
   bool has_variants;  // reduced-precision waves and ePIE are instantiated
 };
 

@@ -150,11 +150,24 @@ struct Engine {
     return n;
   }
 
+  static unsigned take_exchange_timeouts() {
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_exchange_timeouts, sizeof(v)) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    if (v) {
+      const unsigned z = 0;
+      if (cudaMemcpyToSymbol(g_exchange_timeouts, &z, sizeof(z)) != cudaSuccess) cudaGetLastError();
+    }
+    return v;
+  }
+
   static const EngineOps* ops() {
     static const EngineOps o = {TL::N,         TL::G,      TL::T,       TL::R1,      TL::R2,
                                 TL::SMEM,      &probe_spectrum, &forward, &adjoint,  &probe_grad,
                                 &fft_debug,    &modesum,   &loss,       &seed,       &resident_clusters,
-                                &adjoint_pos,  &resident_pos, ALLV};
+                                &adjoint_pos,  &resident_pos, &take_exchange_timeouts, ALLV};
     return &o;
   }
 };

@@ -345,6 +345,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_forward(const __grid_consta
     TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{},
                                                [&](int pu, int pv, float2& v) { Aout[pu * N + pv] = v; });
   }
+  // no CTA leaves while its partner may still be sending to it
+  TL::sync_cluster();
 }
 
 // Adjoint.  STORE: psi_s come from the forward's store; the seed is
@@ -392,6 +394,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_consta
     TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
     adjoint_chain<TL, V>(sm, rank, D, g, waves);
   }
+  // no CTA leaves while its partner may still be sending to it
+  TL::sync_cluster();
 }
 
 // Loss + adjoint with the entry waves recomputed, one cluster per scan
@@ -477,6 +481,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
       adjoint_chain<TL, V>(sm, rank, D, g, slot + k * wstride);
     }
   }
+  // no CTA leaves while its partner may still be sending to it
+  TL::sync_cluster();
 }
 
 // Probe spectra P^_k = F P_k in spectral slot order (one item per mode).
@@ -500,6 +506,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_spectrum(const float2
     TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{},
                                                [&](int pu, int pv, float2& v) { out[pu * N + pv] = v; });
   }
+  // no CTA leaves while its partner may still be sending to it
+  TL::sync_cluster();
 }
 
 // Probe gradient g_P_k = F^-1 g_P^_k (natural order); ACC adds to gP.
@@ -527,6 +535,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_grad(const float2* __
                                             out[r * N + c] = acc ? cadd(out[r * N + c], x) : x;
                                           });
   }
+  // no CTA leaves while its partner may still be sending to it
+  TL::sync_cluster();
 }
 
 // Stand-alone 2-D DFT of natural-order arrays through the tile (tests).
@@ -561,6 +571,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_fft_debug(const float2* __r
                                             [&](int r, int c, float2& v, const NoPre::type&) { y[r * N + c] = v; });
     }
   }
+  // no CTA leaves while its partner may still be sending to it
+  TL::sync_cluster();
 }
 
 }  // namespace ptycho

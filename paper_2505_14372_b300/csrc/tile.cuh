@@ -22,8 +22,10 @@
 // is a block transpose across the cluster: element (CTA c, block b, row r,
 // column cc) moves to (CTA b, block c, r, cc); it is fused into the last
 // stage of a row pass (row -> column) and of an inverse column pass (column
-// -> row), written with st.shared::cluster into the partner's smem between
-// two cluster barriers.
+// -> row).  For G = 2 the off-diagonal block goes with st.async into the
+// partner's idle buffer and is counted on the partner's mbarrier (no cluster
+// barrier per switch); G = 4 stages it in registers and writes it with
+// st.shared::cluster between two cluster barriers.
 //
 // Bank conflicts: slot (b, r, cc) sits at b*ROWS^2 + r*ROWS + (cc ^ f) with
 // f = (R1 r + NB b + cc / R2) mod 16, NB = ROWS / R2.  Lanes of a half-warp
@@ -71,6 +73,46 @@ __device__ __forceinline__ void red_add(float2* p, float2 v) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// ---- mbarrier-signalled exchange between the two CTAs of a 192x192 tile --
+// A layout switch writes the off-diagonal block straight into the partner's
+// idle buffer with st.async, each store counting its bytes on the partner's
+// mbarrier; the partner waits on that mbarrier (expected bytes = one block)
+// instead of both CTAs meeting at a cluster barrier.  No release fence is
+// needed on the sending side.  Reuse of a buffer is ordered by the data
+// flow: a CTA writes its partner's buffer only after it has received the
+// partner's data of the opposite switch, which the partner sends after its
+// last read of that buffer.
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ uint64_t mbar_arrive(uint32_t bar) {
+  uint64_t st;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(bar) : "memory");
+  return st;
+}
+__device__ __forceinline__ uint64_t mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  uint64_t st;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;" : "=l"(st) : "r"(bar), "r"(bytes) : "memory");
+  return st;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint64_t st) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "l"(st)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void st_async(uint32_t addr, float2 v, uint32_t remote_bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "r"(remote_bar)
+               : "memory");
+}
+// exchange waits that gave up (bounded wait); read and cleared by the host
+static __device__ unsigned g_exchange_timeouts;
+constexpr unsigned kExchangeSpin = 1u << 22;
+
 struct NoLoad {
   __device__ float2 operator()(int, int) const { return make_float2(0.f, 0.f); }
 };
@@ -103,8 +145,12 @@ struct Tile {
   static constexpr int TC = ROWS * R1;               // contiguous-stage tasks (R2 elements)
   static constexpr int SPT = (TS + T - 1) / T;       // strided tasks per thread (last may idle)
   static constexpr int CPT = (TC + T - 1) / T;       // contiguous tasks per thread
-  // smem: wave, twS[N], twC[N], rampY[N], rampX[N], chirp[2][N], fsq[N] (int)
-  static constexpr size_t SMEM = sizeof(float2) * (WAVE + 6 * N) + sizeof(int) * N;
+  // smem: wave, twS[N], twC[N], rampY[N], rampX[N], chirp[2][N], fsq[N] (int),
+  // then (G == 2) the two exchange mbarriers: [0] row-layout block arrived,
+  // [1] column-layout block arrived
+  static constexpr size_t BAR_OFF = sizeof(float2) * (WAVE + 6 * N) + sizeof(int) * N;
+  static constexpr size_t SMEM = BAR_OFF + (XB ? 16 : 0);
+  static_assert(BAR_OFF % 8 == 0, "mbarrier alignment");
   static_assert(N == R1 * R2 && R2 % 16 == 0, "N = R1 R2 with R2 a multiple of 16");
   static_assert(N % G == 0 && ROWS % R2 == 0 && ROWS % 16 == 0, "block split");
   static_assert(T % 32 == 0, "whole warps");
@@ -142,7 +188,36 @@ struct Tile {
   // Twiddles W_N^(n2 k1) = exp(-2 pi i n2 k1 / N): twS[k1*R2 + n2] (strided
   // stage, lanes over n2) and twC[n2*R1 + k1] (contiguous stage, lanes over
   // k1); fsq[p] = freq(nat(p))^2 for the band limit.
+  __device__ static uint32_t bar_addr(const float2* wave, int which) {
+    return smem_u32(wave) + (uint32_t)BAR_OFF + 8u * (uint32_t)which;
+  }
+  // Waits until the partner's block for this layout switch has arrived
+  // (bounded: gives up after kExchangeSpin polls and flags it), then makes
+  // this CTA's own writes of the stage visible to all its threads.
+  __device__ static void exchange_wait(const float2* wave, int which) {
+    const uint32_t bar = bar_addr(wave, which);
+    uint64_t tok = 0;
+    if ((threadIdx.x & 31) == 0) tok = threadIdx.x == 0 ? mbar_arrive_tx(bar, BLK * 8) : mbar_arrive(bar);
+    tok = __shfl_sync(0xffffffffu, tok, 0);
+    unsigned it = 0;
+    while (!mbar_try_wait(bar, tok)) {
+      if (++it > kExchangeSpin) {
+        atomicOr(&g_exchange_timeouts, 1u);
+        break;
+      }
+    }
+    __syncthreads();
+  }
+
   __device__ static void init_tables(float2* twS, float2* twC, int* fsq) {
+    if constexpr (XB) {
+      if (threadIdx.x == 0) {
+        const float2* wave = twS - WAVE;
+        mbar_init(bar_addr(wave, 0), T / 32);
+        mbar_init(bar_addr(wave, 1), T / 32);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
+    }
     for (int i = threadIdx.x; i < N; i += T) {
       const int k1 = i / R2, n2 = i % R2;
       double s, c;
@@ -264,13 +339,13 @@ struct Tile {
         } else {
           // off-diagonal block -> the partner's idle column-layout buffer
           const uint32_t base = cluster_map(w0, (uint32_t)b);
+          const uint32_t rbar = cluster_map(bar_addr(wave, 1), (uint32_t)b);
 #pragma unroll
-          for (int i = 0; i < R2; ++i) st_cluster(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + i), x[i]);
+          for (int i = 0; i < R2; ++i) st_async(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + i), x[i], rbar);
         }
       }
       if constexpr (DIR < 0 && G > 1) {
-        cluster_arrive_release();
-        cluster_wait();
+        exchange_wait(wave, 1);
       } else {
         __syncthreads();
       }
@@ -316,10 +391,13 @@ struct Tile {
       cluster_wait();
     } else {
       const uint32_t w0 = smem_u32(wave);
-      uint32_t base[G];
+      uint32_t base[G], rbar[G];
       if constexpr (DIR > 0 && XB) {
 #pragma unroll
-        for (int b = 0; b < G; ++b) base[b] = cluster_map(w0, (uint32_t)b);
+        for (int b = 0; b < G; ++b) {
+          base[b] = cluster_map(w0, (uint32_t)b);
+          rbar[b] = cluster_map(bar_addr(wave, 0), (uint32_t)b);
+        }
       }
 #pragma unroll 1
       for (int t = 0; t < SPT; ++t) {
@@ -341,13 +419,12 @@ struct Tile {
           for (int i = 0; i < R1; ++i) {
             const int b = i / NB, r = n2 + R2 * (i % NB);
             if (G == 1 || b == rank) wave[rslot(rank, b, r, cc)] = x[i];
-            else st_cluster(base[b] + 8u * (uint32_t)rslot(b, rank, r, cc), x[i]);  // partner's idle buffer
+            else st_async(base[b] + 8u * (uint32_t)rslot(b, rank, r, cc), x[i], rbar[b]);  // partner's idle buffer
           }
         }
       }
       if constexpr (DIR > 0 && G > 1) {
-        cluster_arrive_release();
-        cluster_wait();
+        exchange_wait(wave, 0);
       } else {
         __syncthreads();
       }
