@@ -27,12 +27,15 @@
 // barrier per switch); G = 4 stages it in registers and writes it with
 // st.shared::cluster between two cluster barriers.
 //
-// Bank conflicts: slot (b, r, cc) sits at b*ROWS^2 + r*ROWS + (cc ^ f) with
-// f = (R1 r + NB b + cc / R2) mod 16, NB = ROWS / R2.  Lanes of a half-warp
-// then hit 16 distinct bank pairs in all four stage patterns: the strided
-// and column stages walk 16 consecutive cc of one row (f constant, the XOR
-// permutes them), and the row-contiguous stage has lanes (r, k1) with
-// f = (R1 r + k1) mod 16 = lane id mod 16.
+// Bank conflicts: slot (b, r, cc) sits at b*ROWS^2 + r*ROWS +
+// 2((cc >> 1) ^ f) + (cc & 1) with f = (R1 r + NB b + cc / R2) mod 8,
+// NB = ROWS / R2: the XOR permutes 16-byte column pairs, so columns cc, cc+1
+// (cc even) stay adjacent and in order.  The strided and column stages walk
+// 16 consecutive cc of one row with 8-byte accesses (f constant: 16
+// distinct bank pairs per half-warp); the row-contiguous stage reads and
+// writes its 16 consecutive columns as 8 16-byte pairs, and its lanes
+// (r, k1) have f = (R1 r + k1) mod 8 = lane id mod 8, so each quarter-warp
+// hits 8 distinct 16-byte bank groups.
 #pragma once
 #include <stdint.h>
 
@@ -109,6 +112,16 @@ __device__ __forceinline__ void st_async(uint32_t addr, float2 v, uint32_t remot
                "f"(v.x), "f"(v.y), "r"(remote_bar)
                : "memory");
 }
+__device__ __forceinline__ void st_async2(uint32_t addr, float2 a, float2 b, uint32_t remote_bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+               "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "r"(remote_bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_cluster2(uint32_t addr, float2 a, float2 b) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a.x), "f"(a.y), "f"(b.x),
+               "f"(b.y)
+               : "memory");
+}
 // exchange waits that gave up (bounded wait); read and cleared by the host
 static __device__ unsigned g_exchange_timeouts;
 constexpr unsigned kExchangeSpin = 1u << 22;
@@ -165,12 +178,21 @@ struct Tile {
   // the row layout (COL = false) or the column layout (COL = true)
   template <bool COL>
   __device__ static __forceinline__ int slot(int rank, int b, int r, int cc) {
-    const int f = (R1 * r + NB * b + cc / R2) & 15;
+    const int f = (R1 * r + NB * b + cc / R2) & 7;
     int base;
     if constexpr (G == 1) base = 0;
     else if constexpr (XB) base = b == rank ? 0 : (COL ? 2 * BLK : BLK);
     else base = b * BLK;
-    return base + r * ROWS + (cc ^ f);
+    return base + r * ROWS + (((cc >> 1) ^ f) << 1) + (cc & 1);
+  }
+  // 16-byte pair (slots s, s + 1) holding columns cc, cc + 1 (cc even)
+  __device__ static __forceinline__ void ld_pair(const float2* wave, int s, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(wave + s);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  }
+  __device__ static __forceinline__ void st_pair(float2* wave, int s, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(wave + s) = make_float4(a.x, a.y, b.x, b.y);
   }
   // full barrier over the CTAs that share one wavefield
   __device__ static void sync_cluster() {
@@ -290,7 +312,7 @@ struct Tile {
         const int r = id / R1, k1 = id % R1;
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
 #pragma unroll
-        for (int i = 0; i < R2; ++i) x[t][i] = wave[rslot(rank, b, r, cc0 + i)];
+        for (int m = 0; m < R2; m += 2) ld_pair(wave, rslot(rank, b, r, cc0 + m), x[t][m], x[t][m + 1]);
       }
       // the DFTs consume every loaded value, so the loads have completed
       // before this thread arrives: the partner may then overwrite them
@@ -307,11 +329,12 @@ struct Tile {
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
         if (b == rank) {
 #pragma unroll
-          for (int i = 0; i < R2; ++i) wave[cslot(rank, rank, r, cc0 + i)] = x[t][i];
+          for (int m = 0; m < R2; m += 2) st_pair(wave, cslot(rank, rank, r, cc0 + m), x[t][m], x[t][m + 1]);
         } else {
           const uint32_t base = cluster_map(w0, (uint32_t)b);
 #pragma unroll
-          for (int i = 0; i < R2; ++i) st_cluster(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + i), x[t][i]);
+          for (int m = 0; m < R2; m += 2)
+            st_cluster2(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + m), x[t][m], x[t][m + 1]);
         }
       }
       cluster_arrive_release();
@@ -326,7 +349,7 @@ struct Tile {
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
         float2 x[R2];
 #pragma unroll
-        for (int i = 0; i < R2; ++i) x[i] = wave[rslot(rank, b, r, cc0 + i)];
+        for (int m = 0; m < R2; m += 2) ld_pair(wave, rslot(rank, b, r, cc0 + m), x[m], x[m + 1]);
         Dft<R2, DIR>::run(x);
         if constexpr (DIR > 0) {
 #pragma unroll
@@ -335,13 +358,14 @@ struct Tile {
         if (DIR > 0 || G == 1 || b == rank) {
           // in place (row layout) or the diagonal block (same slots in both layouts)
 #pragma unroll
-          for (int i = 0; i < R2; ++i) wave[rslot(rank, b, r, cc0 + i)] = x[i];
+          for (int m = 0; m < R2; m += 2) st_pair(wave, rslot(rank, b, r, cc0 + m), x[m], x[m + 1]);
         } else {
           // off-diagonal block -> the partner's idle column-layout buffer
           const uint32_t base = cluster_map(w0, (uint32_t)b);
           const uint32_t rbar = cluster_map(bar_addr(wave, 1), (uint32_t)b);
 #pragma unroll
-          for (int i = 0; i < R2; ++i) st_async(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + i), x[i], rbar);
+          for (int m = 0; m < R2; m += 2)
+            st_async2(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + m), x[m], x[m + 1], rbar);
         }
       }
       if constexpr (DIR < 0 && G > 1) {
