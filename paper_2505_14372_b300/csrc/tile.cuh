@@ -262,6 +262,14 @@ struct Tile {
   template <bool FROM_SMEM, bool TO_SMEM, class Load, class Pre, class Op>
   __device__ static void row_strided(float2* wave, const float2* twS, int rank, const Load& load, const Pre& pre,
                                      const Op& op) {
+    // when T is a multiple of R2 every task of a thread has the same n2, so
+    // its twiddles are loaded once per stage
+    constexpr bool HOIST = TO_SMEM && (T % R2 == 0);
+    float2 tw[R1];
+    if constexpr (HOIST) {
+#pragma unroll
+      for (int k = 1; k < R1; ++k) tw[k] = twS[k * R2 + (int)(threadIdx.x % R2)];
+    }
 #pragma unroll 1
     for (int t = 0; t < SPT; ++t) {
       const int id = threadIdx.x + t * T;
@@ -288,7 +296,10 @@ struct Tile {
       if constexpr (TO_SMEM) {
         Dft<R1, -1>::run(x);
 #pragma unroll
-        for (int k = 1; k < R1; ++k) x[k] = cmul(x[k], twS[k * R2 + n2]);
+        for (int k = 1; k < R1; ++k) {
+          if constexpr (HOIST) x[k] = cmul(x[k], tw[k]);
+          else x[k] = cmul(x[k], twS[k * R2 + n2]);
+        }
 #pragma unroll
         for (int i = 0; i < R1; ++i) {
           const int col = n2 + R2 * i;
@@ -341,6 +352,14 @@ struct Tile {
       cluster_wait();
     } else {
       const uint32_t w0 = smem_u32(wave);
+      // when T is a multiple of R1 every task of a thread has the same k1, so
+      // the inverse stage's twiddles are loaded once per stage
+      constexpr bool HOIST = DIR > 0 && (T % R1 == 0);
+      float2 tw[R2];
+      if constexpr (HOIST) {
+#pragma unroll
+        for (int i = 1; i < R2; ++i) tw[i] = twC[i * R1 + (int)(threadIdx.x % R1)];
+      }
 #pragma unroll 1
       for (int t = 0; t < CPT; ++t) {
         const int id = threadIdx.x + t * T;
@@ -353,7 +372,10 @@ struct Tile {
         Dft<R2, DIR>::run(x);
         if constexpr (DIR > 0) {
 #pragma unroll
-          for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
+          for (int i = 1; i < R2; ++i) {
+            if constexpr (HOIST) x[i] = cmulc(x[i], tw[i]);
+            else x[i] = cmulc(x[i], twC[i * R1 + k1]);
+          }
         }
         if (DIR > 0 || G == 1 || b == rank) {
           // in place (row layout) or the diagonal block (same slots in both layouts)
