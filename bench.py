@@ -154,6 +154,22 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's): an all-reduce MAX, a no-op for one rank."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the job's time."""
+    return world * units_per_rank / seconds
+
+
 def fft_flops(NP):
     return 5.0 * NP * math.log2(NP)
 
@@ -464,12 +480,10 @@ def main():
     ctx.check_status()
     ktimes = ctx.kernel_times()
     ctx.set_timing(False)
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    ms_max = max_over_ranks(ms, world, dev)
     if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
         dist.barrier()
-    ms_max = float(t_max.item())
-    value = world * B * args.steps / (ms_max / 1e3)
+    value = job_rate(B * args.steps, world, ms_max / 1e3)
     loss_last = stats.tolist()
 
     # ---- end to end through the C-ABI with host buffers (pinned), copies timed
@@ -499,10 +513,8 @@ def main():
         else:
             ctx.step_host(Od, Pd, st, opt, pos_host[i * B:(i + 1) * B], I_host[i * B:(i + 1) * B])
     t_e2e = time.perf_counter() - t0
-    te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * B * e2e_steps / float(te.item()), "unit": "positions/s",
+    te = max_over_ranks(t_e2e, world, dev)
+    e2e = {"value": job_rate(B * e2e_steps, world, te), "unit": "positions/s",
            "h2d_bytes_per_step": B * 2 * 4 + B * wl.N * wl.N * 4,
            "d2h_bytes_per_step": 8 if args.engine == "epie" else 16,
            "api": ("ptycho_epie_step after pinned host-to-device copies" if args.engine == "epie"
