@@ -73,6 +73,18 @@ repository's list of readings):
       adjoint propagator conj(H); the probe update of each mode is the
       group mean of the unshifted entry-plane updates (the paper's mean is
       over the group); c and eps are the noise model's.
+  R17 LSQML (§3.3.2): the detector update is ePIE's; the object direction
+      is summed over the group and the modes; the step sizes alpha are
+      least-squares steps per position (and per slice for the object), with
+      the object direction restricted to the position's window in them; the
+      probe update follows the object's at the entry plane (the paper says
+      only that it is computed similarly): direction conj(O_0) chi_0 moved
+      to the probe frame by the inverse sub-pixel shift, normaliser the
+      transmission prod_s |O_s|^2 summed over the group's positions, step
+      sizes from the exit-wave change O_0 S_j dP; the normalising sums are the
+      group's own unless running sums of a previous iteration are passed in
+      (the paper keeps them from the previous iteration); delta_O, delta_P
+      and gamma are absolute.
 """
 from __future__ import annotations
 
@@ -92,7 +104,7 @@ __all__ = [
     "shift_probe", "bandlimit_mask", "propagator", "propagate",
     "forward", "forward_waves", "loss_terms", "loss_value", "gradient",
     "adam_update", "step", "position_gradient", "vjp", "GAUSSIAN", "regularizers",
-    "round_storage", "epie_update",
+    "round_storage", "epie_update", "lsqml_update", "lsqml_directions", "transmission",
 ]
 
 
@@ -451,6 +463,118 @@ def epie_update(O, P, pos, I_exp, g: Geom, beta_O=1.0, beta_P=1.0, tiny=1e-30):
     O_new = O + beta_O * dO
     P_new = P + beta_P * idft2(dPhat) / max(B, 1)
     return O_new, P_new, loss
+
+
+# ------------------------------------------------------------ LSQML (§3.3.2)
+
+def transmission(O, n, h, w):
+    """Product over slices of |O_s|^2 on the window at integer origin n: how
+    transparent the object is to each pixel of the probe (R17)."""
+    t = np.ones((h, w))
+    for s in range(O.shape[0]):
+        t *= np.abs(_patch(O, s, n, h, w)) ** 2
+    return t
+
+
+def lsqml_directions(O, P, pos, I_exp, g: Geom):
+    """Step 1 of the LSQML update (R17): for one group, the object and probe
+    update directions summed over positions and modes (NO [S,H,W], NP [K,h,w],
+    probe frame), the group's illumination W [S,H,W] and transmission
+    T [h,w], the exit-plane updates chi [B,S,K,h,w] of every slice, and the
+    forward pass (psis, n, d) and loss they came from."""
+    if g.loss != AMPLITUDE:
+        raise ValueError("LSQML uses the amplitude / Anscombe modulus update")
+    psis, A, n, d = forward_waves(O, P, pos, g)
+    O = np.asarray(O, dtype=np.complex128)
+    E = np.asarray(I_exp, dtype=np.float64).reshape(-1, g.h, g.w)
+    Hs = _props(g)
+    B = n.shape[0]
+    S, K, h, w = g.S, g.K, g.h, g.w
+    NO = np.zeros_like(O)                       # object directions, summed
+    NP_ = np.zeros((K, h, w), np.complex128)    # probe directions, summed (probe frame)
+    W = np.zeros(O.shape)                       # illumination of this group
+    T = np.zeros((h, w))                        # transmission of this group
+    chis = np.zeros((B, S, K, h, w), np.complex128)  # exit-plane updates per slice
+    loss = 0.0
+    for j in range(B):
+        I = np.sum(np.abs(A[j]) ** 2, axis=0)
+        loss += float(np.sum(loss_terms(I, E[j], g)[0]))
+        m = np.sqrt(E[j] + g.c) / (g.eps + np.sqrt(I + g.c)) - 1.0
+        y0, x0 = n[j]
+        T += transmission(O, n[j], h, w)
+        for k in range(K):
+            chi = idft2_ortho(m * A[j, k])
+            for s in range(S - 1, -1, -1):
+                chis[j, s, k] = chi
+                NO[s, y0:y0 + h, x0:x0 + w] += np.conj(psis[j, s, k]) * chi
+                W[s, y0:y0 + h, x0:x0 + w] += np.abs(psis[j, s, k]) ** 2
+                chi = np.conj(_patch(O, s, n[j], h, w)) * chi
+                if s > 0:
+                    chi = idft2(np.conj(Hs[s - 1]) * dft2(chi))
+            NP_[k] += idft2(np.conj(shift_ramp(d[j, 0], d[j, 1], h, w)) * dft2(chi))
+    return NO, NP_, W, T, chis, psis, n, d, loss
+
+
+def lsqml_update(O, P, pos, I_exp, g: Geom, beta_O=1.0, beta_P=1.0, delta_O=0.0, delta_P=0.0, gamma=0.0,
+                 illum=None, trans=None):
+    """One LSQML update of O and P from one group of positions (R17), in the
+    order of §3.3.2:
+      1. exit-plane updates chi of every position and mode from the
+         generalised modulus constraint (as ePIE), carried back through the
+         slices: at slice s the object direction conj(psi_s) chi_s and the
+         illumination direction conj(O_s) chi_s, the latter propagated back
+         (conj(H)) to become chi_{s-1}; at the entry plane it is unshifted
+         into the probe frame;
+      2. the object direction summed over the group and modes, divided by the
+         illumination sum_{j,k} |psi_s|^2 + delta_O (object frame); the probe
+         direction summed over the group, divided by the transmission
+         sum_j prod_s |O_s|^2 + delta_P (probe frame); `illum` [S,H,W] and
+         `trans` [h,w] replace these sums when given (the running sums of a
+         previous iteration);
+      3. per position j, least-squares step sizes
+         alpha_{s,j} = sum_{r,k} Re[chi_s conj(dO_s psi_s)] / (sum |dO_s psi_s|^2 + gamma)
+         alpha_{P,j} = sum_{r,k} Re[chi_0 conj(O_0 S_j dP_k)] / (sum |O_0 S_j dP_k|^2 + gamma),
+         S_j the position's sub-pixel shift;
+      4. O_s += beta_O dO_s sum_j alpha_{s,j} w_{s,j} / sum_j w_{s,j}, with
+         w_{s,j} = sum_k |psi_{s,k,j}|^2; P_k += beta_P dP_k sum_j alpha_{P,j} t_j /
+         sum_j t_j, with t_j the transmission of position j (zero weight sums
+         leave the pixel unchanged).
+    The noise model must be the amplitude one.  Returns
+    (O_new, P_new, loss, illum_group [S,H,W], trans_group [h,w])."""
+    NO, NP_, W, T, chis, psis, n, d, loss = lsqml_directions(O, P, pos, I_exp, g)
+    O = np.asarray(O, dtype=np.complex128)
+    P = np.asarray(P, dtype=np.complex128)
+    B = n.shape[0]
+    S, K, h, w = g.S, g.K, g.h, g.w
+    Wd = W if illum is None else np.asarray(illum, dtype=np.float64)
+    Td = T if trans is None else np.asarray(trans, dtype=np.float64)
+    # pixels no position of the group reaches keep a zero direction
+    dO = np.divide(NO, Wd + delta_O, out=np.zeros_like(NO), where=(Wd + delta_O) > 0)
+    dP = np.divide(NP_, (Td + delta_P)[None], out=np.zeros_like(NP_), where=((Td + delta_P) > 0)[None])
+    AW = np.zeros(O.shape)
+    AT = np.zeros((h, w))
+    for j in range(B):
+        y0, x0 = n[j]
+        for s in range(S):
+            dOs = dO[s, y0:y0 + h, x0:x0 + w]
+            num = den = 0.0
+            for k in range(K):
+                q = dOs * psis[j, s, k]
+                num += float(np.sum(np.real(chis[j, s, k] * np.conj(q))))
+                den += float(np.sum(np.abs(q) ** 2))
+            a = num / (den + gamma) if den + gamma > 0 else 0.0
+            AW[s, y0:y0 + h, x0:x0 + w] += a * np.sum(np.abs(psis[j, s]) ** 2, axis=0)
+        O0 = _patch(O, 0, n[j], h, w)
+        num = den = 0.0
+        for k in range(K):
+            q = O0 * shift_probe(dP[k:k + 1], d[j, 0], d[j, 1])[0]
+            num += float(np.sum(np.real(chis[j, 0, k] * np.conj(q))))
+            den += float(np.sum(np.abs(q) ** 2))
+        aP = num / (den + gamma) if den + gamma > 0 else 0.0
+        AT += aP * transmission(O, n[j], h, w)
+    O_new = O + beta_O * dO * np.divide(AW, W, out=np.zeros_like(AW), where=W > 0)
+    P_new = P + beta_P * dP * np.divide(AT, T, out=np.zeros_like(AT), where=T > 0)[None]
+    return O_new, P_new, loss, W, T
 
 
 # ---------------------------------------------------- regularisers (§3.4)
