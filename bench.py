@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--rate", type=float, default=16.0, help="mean request arrivals per second")
     ap.add_argument("--precision", action="store_true",
                     help="relative L2 error of every DFT mode against the FP64 oracle on a 4-position sub-problem")
-    ap.add_argument("--engine", default="gd", choices=["gd", "epie"],
+    ap.add_argument("--engine", default="gd", choices=["gd", "epie", "lsqml"],
                     help="gd: gradient descent with Adam (ptycho_step); epie: the ePIE / 3PIE update "
-                         "(ptycho_epie_step, amplitude noise model)")
+                         "(ptycho_epie_step); lsqml: the LSQML update (ptycho_lsqml_step); the last two use "
+                         "the amplitude noise model")
     ap.add_argument("--positions", type=int, default=0,
                     help="use only the first P scan positions (small profiling cases; the line says so)")
     ap.add_argument("--group", type=int, default=0,
@@ -424,7 +425,7 @@ def main():
         nx = wl.scan[1]
         wl = dataclasses.replace(wl, scan=(max(1, min(args.positions, wl.P) // nx), nx))
     geom = workload_geometry(wl, args.waves, args.dft, args.wave_prec)
-    if args.engine == "epie":  # ePIE's modulus update belongs to the amplitude model
+    if args.engine in ("epie", "lsqml"):  # their modulus update belongs to the amplitude model
         geom.loss, geom.eps, geom.c = "amplitude", 1e-3, 0.0
     B = wl.B
 
@@ -450,9 +451,13 @@ def main():
     def group(i):
         return idx_all[i * B:(i + 1) * B]
 
+    lsq = dict(beta_O=0.5, beta_P=0.5, delta_O=1e-2, delta_P=1e-2, gamma=1e-6)
+
     def one_step(i):
         if args.engine == "epie":
             ctx.epie_step(Od, Pd, pos_d, Iexp_d, group(i), beta_O=0.5, beta_P=0.5, loss=stats[:1])
+        elif args.engine == "lsqml":
+            ctx.lsqml_step(Od, Pd, pos_d, Iexp_d, group(i), loss=stats[:1], **lsq)
         else:
             ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, group(i), stats=stats)
 
@@ -497,8 +502,8 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    if args.engine == "epie":
-        # the public ePIE call takes device arrays: the timed region copies
+    if args.engine in ("epie", "lsqml"):
+        # the public ePIE / LSQML calls take device arrays: the timed region copies
         # each group's positions and patterns in and reads its loss back
         pos_g = torch.empty((B, 2), dtype=torch.float32, device=dev)
         I_g = torch.empty((B, wl.N, wl.N), dtype=torch.float32, device=dev)
@@ -506,19 +511,22 @@ def main():
         torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        if args.engine == "epie":
+        if args.engine in ("epie", "lsqml"):
             pos_g.copy_(pos_host[i * B:(i + 1) * B], non_blocking=True)
             I_g.copy_(I_host[i * B:(i + 1) * B], non_blocking=True)
-            float(ctx.epie_step(Od, Pd, pos_g, I_g, ident, beta_O=0.5, beta_P=0.5).item())
+            if args.engine == "epie":
+                float(ctx.epie_step(Od, Pd, pos_g, I_g, ident, beta_O=0.5, beta_P=0.5).item())
+            else:
+                float(ctx.lsqml_step(Od, Pd, pos_g, I_g, ident, **lsq).item())
         else:
             ctx.step_host(Od, Pd, st, opt, pos_host[i * B:(i + 1) * B], I_host[i * B:(i + 1) * B])
     t_e2e = time.perf_counter() - t0
     te = max_over_ranks(t_e2e, world, dev)
     e2e = {"value": job_rate(B * e2e_steps, world, te), "unit": "positions/s",
            "h2d_bytes_per_step": B * 2 * 4 + B * wl.N * wl.N * 4,
-           "d2h_bytes_per_step": 8 if args.engine == "epie" else 16,
-           "api": ("ptycho_epie_step after pinned host-to-device copies" if args.engine == "epie"
-                   else "ptycho_step_host (pinned host buffers)")}
+           "d2h_bytes_per_step": 8 if args.engine in ("epie", "lsqml") else 16,
+           "api": (f"ptycho_{args.engine}_step after pinned host-to-device copies"
+                   if args.engine in ("epie", "lsqml") else "ptycho_step_host (pinned host buffers)")}
 
     # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
     dom = max(ktimes, key=lambda k: ktimes[k][0])
@@ -554,7 +562,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(config_dict(wl, args.waves, args.dft, args.wave_prec), engine=args.engine,
-                               **({"loss": "amplitude"} if args.engine == "epie" else {}),
+                               **({"loss": "amplitude"} if args.engine in ("epie", "lsqml") else {}),
                                **({"positions_used": wl.P} if args.positions else {})),
                 "roofline": roofline, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "last_stats": loss_last}

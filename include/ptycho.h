@@ -240,6 +240,40 @@ int ptycho_epie_step(ptycho_ctx* ctx, ptycho_c64* O, ptycho_c64* P, float beta_O
                      const float* pos_all, const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B,
                      double* loss_out, ptycho_stream stream);
 
+/* LSQML options (§3.3.2): step scales of the object and probe updates, the
+ * absolute regularisers of the illumination and transmission normalisers,
+ * and of the step-size denominators. */
+typedef struct {
+  float beta_O, beta_P;
+  float delta_O, delta_P;
+  float gamma;
+} ptycho_lsqml_opt;
+
+/* One LSQML update (§3.3.2) from one group of B scan positions (idx,
+ * pos_all, I_exp_all and n_pos as in ptycho_step), in place.  Every position
+ * of the group sees the same O and P.  From the detector update of §3.1 (as
+ * ePIE) carried back through the slices come the object direction
+ * sum conj(psi_s) chi_s and the probe direction (the entry-plane update
+ * moved to the probe frame), summed over positions and modes and divided by
+ * the illumination sum |psi_s|^2 + delta_O (object frame) and the
+ * transmission sum prod_s |O_s|^2 + delta_P (probe frame); illum_prev
+ * [S][H][W] and trans_prev [N][N] (device, may be NULL) replace those sums
+ * (running sums of a previous iteration).  Per position j the least-squares
+ * steps alpha_{s,j} = sum Re(chi_s conj(dO_s psi_s)) / (sum |dO_s psi_s|^2 + gamma)
+ * and alpha_{P,j} (the same with O_0 S_j dP), then
+ * O_s += beta_O dO_s sum_j alpha_{s,j} w_{s,j} / sum_j w_{s,j} (w = sum_k |psi_s|^2)
+ * and P += beta_P dP sum_j alpha_{P,j} t_j / sum_j t_j (t = prod_s |O_s|^2).
+ * The group's illumination and transmission are added to illum_acc and
+ * trans_acc when given.  Needs the amplitude noise model, recomputed FP32
+ * entry waves and the FFT tile (EINVAL otherwise); allocates its own
+ * buffers (about 16 bytes per object pixel) on the first call.  loss_out
+ * (device double, may be NULL) receives the group's amplitude loss before
+ * the update. */
+int ptycho_lsqml_step(ptycho_ctx* ctx, ptycho_c64* O, ptycho_c64* P, const ptycho_lsqml_opt* opt,
+                      const float* illum_prev, const float* trans_prev, float* illum_acc, float* trans_acc,
+                      const float* pos_all, const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B,
+                      double* loss_out, ptycho_stream stream);
+
 /* Synchronises `stream` and reports (then clears) the device status word:
  * PTYCHO_EOUTOFBOUNDS if any item was skipped since the last check. */
 int ptycho_check(ptycho_ctx* ctx, ptycho_stream stream);

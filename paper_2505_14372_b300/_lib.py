@@ -38,6 +38,11 @@ class Opt(C.Structure):
                 ("reg_obj_tv", C.c_float), ("reg_obj_layers_tv", C.c_float), ("reg_tv_eps", C.c_float)]
 
 
+class LsqmlOpt(C.Structure):
+    _fields_ = [("beta_O", C.c_float), ("beta_P", C.c_float), ("delta_O", C.c_float), ("delta_P", C.c_float),
+                ("gamma", C.c_float)]
+
+
 class Adam(C.Structure):
     _fields_ = [("mO", C.c_void_p), ("vO", C.c_void_p), ("mP", C.c_void_p), ("vP", C.c_void_p),
                 ("t", C.c_int64)]
@@ -82,6 +87,7 @@ SIGNATURES = {
     "ptycho_step_host": (I32, [P_, P_, P_, C.POINTER(Adam), C.POINTER(Opt), P_, P_, I32,
                                C.POINTER(C.c_double), C.POINTER(C.c_double), P_]),
     "ptycho_epie_step": (I32, [P_, P_, P_, C.c_float, C.c_float, P_, P_, I32, P_, I32, P_, P_]),
+    "ptycho_lsqml_step": (I32, [P_, P_, P_, C.POINTER(LsqmlOpt), P_, P_, P_, P_, P_, P_, I32, P_, I32, P_, P_]),
     "ptycho_check": (I32, [P_, P_]),
     "ptycho_make_groups": (I32, [I32, I32, C.c_uint64, C.c_int64, I32, P_, P_]),
     "ptycho_set_timing": (I32, [P_, I32]),

@@ -202,6 +202,31 @@ class Context:
                                      _ptr(I_exp_all), n_pos, _ptr(idx), B, _ptr(loss), _stream()))
         return loss
 
+    def lsqml_step(self, O, P, pos_all, I_exp_all, idx, beta_O=1.0, beta_P=1.0, delta_O=0.0, delta_P=0.0,
+                   gamma=0.0, illum_prev=None, trans_prev=None, illum_acc=None, trans_acc=None, loss=None):
+        """One LSQML update (ptycho_lsqml_step) of O and P in place from the
+        group idx; illum_* [S, H, W] and trans_* [N, N] are optional float32
+        device tensors (running sums in, the group's sums added out).
+        Returns a device float64 tensor [loss before the update]."""
+        B = idx.shape[0]
+        _need(idx, torch.int32, (B,), "idx")
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float64, device=O.device)
+        g = self.geom
+        n_pos = pos_all.shape[0]
+        _need(pos_all, torch.float32, (n_pos, 2), "pos_all")
+        _need(I_exp_all, torch.float32, (n_pos, g.N, g.N), "I_exp_all")
+        for t, shape, name in ((illum_prev, (g.S, g.H, g.W), "illum_prev"), (illum_acc, (g.S, g.H, g.W), "illum_acc"),
+                               (trans_prev, (g.N, g.N), "trans_prev"), (trans_acc, (g.N, g.N), "trans_acc")):
+            if t is not None:
+                _need(t, torch.float32, shape, name)
+        opt = _lib.LsqmlOpt(beta_O, beta_P, delta_O, delta_P, gamma)
+        ptr = lambda t: _ptr(t) if t is not None else None
+        check(lib().ptycho_lsqml_step(self.h, _ptr(O), _ptr(P), C.byref(opt), ptr(illum_prev), ptr(trans_prev),
+                                      ptr(illum_acc), ptr(trans_acc), _ptr(pos_all), _ptr(I_exp_all), n_pos,
+                                      _ptr(idx), B, _ptr(loss), _stream()))
+        return loss
+
     def step_host(self, O, P, state: AdamState, opt, pos_host: np.ndarray, I_exp_host):
         """Step with the group's positions/patterns in host memory (numpy or
         pinned CPU torch tensors); returns (loss, gnorm) as floats."""

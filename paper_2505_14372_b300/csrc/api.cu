@@ -41,8 +41,9 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   L.w = take((size_t)B * NP * 4);
   L.gPhat = take((size_t)g.K * NP * 8);
   // loss partials: block sums of the loss kernel, or one per position for
-  // the position-major kernel; then regulariser and gradient-norm partials
-  L.partials = take((size_t)(std::max(ptycho::kLossBlocks, B) + 3 * ptycho::kNormBlocks + 8) * 8);
+  // the position-major kernel (two passes' worth for LSQML); then regulariser
+  // and gradient-norm partials
+  L.partials = take((size_t)(std::max(ptycho::kLossBlocks, 2 * B) + 3 * ptycho::kNormBlocks + 8) * 8);
   L.stats = take(4 * 8);
   L.stage_pos = take((size_t)B * 2 * 4);
   L.stage_I = take((size_t)B * NP * 4);
@@ -50,8 +51,9 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   L.wmax = take((size_t)B * g.K * g.S * 4);
   const size_t esize = g.wave_prec ? 4 : 8;  // entry-wave copies: complex64 or two 16-bit parts
   // stored: every item's entry waves; recomputed: per cluster the entry waves
-  // of all K modes of its position, their far fields and the intensity
-  L.waves = take(store ? (size_t)B * g.K * g.S * NP * esize : (size_t)slots * g.K * g.S * NP * esize);
+  // of all K modes of its position (plus one wave per mode for the LSQML
+  // step pass), their far fields and the intensity
+  L.waves = take(store ? (size_t)B * g.K * g.S * NP * esize : (size_t)slots * g.K * (g.S + 1) * NP * esize);
   L.pA = take(store ? 0 : (size_t)slots * g.K * NP * 8);
   L.pI = take(store ? 0 : (size_t)slots * NP * 4);
   L.total = off;
@@ -118,6 +120,8 @@ struct ptycho_ctx {
   bool store = true;
   int slots = 0;          // recompute slots (clusters of the recompute adjoint)
   int pos_clusters = 0;   // clusters of the position-major loss + adjoint (<= slots)
+  char* lsq = nullptr;    // LSQML buffers, allocated on first use
+  size_t lsq_bytes = 0;
   int res_fwd = 1, res_adj = 1, res_rec = 1;
   // timing
   bool timing = false;
@@ -282,7 +286,7 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
     F.c = (float)c->g.c;
     CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
     LaunchArgs la = one_problem(c, L, d);
-    la.slot_stride = (long long)K * c->g.S * c->NP * (c->g.wave_prec ? 4 : 8);
+    la.slot_stride = (long long)K * (c->g.S + 1) * c->NP * (c->g.wave_prec ? 4 : 8);
     {
       Timed t(c, "adjoint", s);
       CK(c->ops->adjoint_pos(la, F, std::min(B, c->pos_clusters), variant, s));
@@ -420,6 +424,7 @@ int ptycho_destroy(ptycho_ctx* c) {
   }
   for (auto e : c->pool) cudaEventDestroy(e);
   cudaFree(c->arena);
+  cudaFree(c->lsq);
   cudaFree(c->gO);
   cudaFree(c->gP);
   cudaFree(c->status);
@@ -632,6 +637,141 @@ int ptycho_epie_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, float beta_O, 
   CK(ptycho::launch_axpy(reinterpret_cast<float2*>(O), c->gO, (long long)c->g.S * c->g.H * c->g.W, beta_O, s));
   if (beta_P != 0.f)
     CK(ptycho::launch_axpy(reinterpret_cast<float2*>(P), c->gP, (long long)c->g.K * c->NP, beta_P / (float)B, s));
+  return PTYCHO_OK;
+}
+
+int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_lsqml_opt* opt,
+                      const float* illum_prev, const float* trans_prev, float* illum_acc, float* trans_acc,
+                      const float* pos_all, const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B,
+                      double* loss_out, ptycho_stream stream) {
+  int rc = check_call(c, B);
+  if (rc) return rc;
+  if (!O || !P || !opt) return perr(PTYCHO_EINVAL, "NULL object, probe or options");
+  if (B > 0 && (!idx || !pos_all || !I_exp_all)) return perr(PTYCHO_EINVAL, "NULL positions, patterns or idx");
+  if (n_pos < 0) return perr(PTYCHO_EINVAL, "n_pos < 0");
+  if (c->g.loss != PTYCHO_LOSS_AMPLITUDE)
+    return perr(PTYCHO_EINVAL, "LSQML needs the amplitude / Anscombe noise model");
+  if (c->store || c->pos_clusters <= 0 || !c->ops->has_variants || c->g.wave_prec != PTYCHO_PREC_F32)
+    return perr(PTYCHO_EINVAL, "LSQML runs with recomputed FP32 entry waves and the FFT tile");
+  if (!(std::isfinite(opt->beta_O) && std::isfinite(opt->beta_P) && opt->delta_O >= 0.f && opt->delta_P >= 0.f &&
+        opt->gamma >= 0.f))
+    return perr(PTYCHO_EINVAL, "bad LSQML options");
+  if (B == 0) return PTYCHO_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int K = c->g.K, S = c->g.S;
+  const long long NP = c->NP, nO = (long long)S * c->g.H * c->g.W;
+  // buffers: illumination, step-weighted illumination, object direction,
+  // transmission (plain, weighted), probe direction and its spectra, sums
+  const size_t sz_il = align256((size_t)nO * 4), sz_dO = align256((size_t)nO * 8), sz_T = align256((size_t)NP * 4),
+               sz_dP = align256((size_t)K * NP * 8), sz_sum = align256((size_t)c->max_batch * S * 8),
+               sz_sumP = align256((size_t)c->max_batch * 8);
+  const size_t need = 2 * sz_il + sz_dO + 2 * sz_T + 2 * sz_dP + 2 * sz_sum + 2 * sz_sumP;
+  if (!c->lsq) {
+    if (cudaMalloc(&c->lsq, need) != cudaSuccess) {
+      cudaGetLastError();
+      c->lsq = nullptr;
+      return perr(PTYCHO_ENOMEM, "cudaMalloc of " + std::to_string(need) + " LSQML bytes failed");
+    }
+    c->lsq_bytes = need;
+  }
+  char* q = c->lsq;
+  float* il = reinterpret_cast<float*>(q);
+  float* aw = reinterpret_cast<float*>(q += sz_il);
+  float2* dO = reinterpret_cast<float2*>(q += sz_il);
+  float* T = reinterpret_cast<float*>(q += sz_dO);
+  float* AT = reinterpret_cast<float*>(q += sz_T);
+  float2* dP = reinterpret_cast<float2*>(q += sz_T);
+  float2* dPhat = reinterpret_cast<float2*>(q += sz_dP);
+  double* num = reinterpret_cast<double*>(q += sz_dP);
+  double* den = reinterpret_cast<double*>(q += sz_sum);
+  double* numP = reinterpret_cast<double*>(q += sz_sum);
+  double* denP = reinterpret_cast<double*>(q += sz_sumP);
+
+  const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
+  float2* Phat = reinterpret_cast<float2*>(c->arena + L.Phat);
+  float2* gPhat = reinterpret_cast<float2*>(c->arena + L.gPhat);
+  double* partials = reinterpret_cast<double*>(c->arena + L.partials);
+  ptycho::PosArgs F{};
+  F.Iexp = I_exp_all;
+  F.Abuf = reinterpret_cast<float2*>(c->arena + L.pA);
+  F.Ibuf = reinterpret_cast<float*>(c->arena + L.pI);
+  F.lpart = partials;
+  F.model = ptycho::kModelEpie;  // the modulus-update seed
+  F.eps = (float)c->g.eps;
+  F.c = (float)c->g.c;
+  F.gamma = opt->gamma;
+  const int clusters = std::min((int)B, c->pos_clusters);
+  const long long stride = (long long)K * (S + 1) * NP * 8;
+
+  // pass 1: update directions (into gO, gP) and the group's illumination
+  {
+    Timed t(c, "probe_spectrum", s);
+    CK(c->ops->probe_spectrum(reinterpret_cast<const float2*>(P), Phat, K, s));
+  }
+  CK(cudaMemsetAsync(gPhat, 0, (size_t)K * NP * 8, s));
+  CK(cudaMemsetAsync(c->gO, 0, (size_t)nO * 8, s));
+  CK(cudaMemsetAsync(il, 0, (size_t)nO * 4, s));
+  CK(cudaMemsetAsync(T, 0, (size_t)NP * 4, s));
+  CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
+  ProblemDesc d = base_desc(c, L, O, pos_all, idx, B, n_pos);
+  d.gO = c->gO;
+  d.lsq_il = il;
+  LaunchArgs la = one_problem(c, L, d);
+  la.slot_stride = stride;
+  {
+    Timed t(c, "adjoint", s);
+    CK(c->ops->adjoint_pos(la, F, clusters, ptycho::kVarLsqDir, s));
+  }
+  {
+    Timed t(c, "probe_grad", s);
+    CK(c->ops->probe_grad(gPhat, c->gP, K, 0, s));
+  }
+  if (loss_out) CK(ptycho::launch_finalize(partials, B, 0, loss_out, 0, s));
+  {
+    Timed t(c, "lsq_host_terms", s);
+    CK(ptycho::launch_transmission(reinterpret_cast<const float2*>(O), S, c->g.H, c->g.W, c->N, pos_all, idx, n_pos, B,
+                                   nullptr, nullptr, 0.f, T, s));
+    if (illum_acc) CK(ptycho::launch_add(illum_acc, il, nO, s));
+    if (trans_acc) CK(ptycho::launch_add(trans_acc, T, NP, s));
+    CK(ptycho::launch_divide(c->gO, il, illum_prev, opt->delta_O, nO, nO, dO, s));
+    CK(ptycho::launch_divide(c->gP, T, trans_prev, opt->delta_P, (long long)K * NP, NP, dP, s));
+  }
+  {
+    Timed t(c, "probe_spectrum", s);
+    CK(c->ops->probe_spectrum(dP, dPhat, K, s));
+  }
+  // pass 2: per-position step sizes and the step-weighted illumination
+  CK(cudaMemsetAsync(num, 0, (size_t)B * S * 8, s));
+  CK(cudaMemsetAsync(den, 0, (size_t)B * S * 8, s));
+  CK(cudaMemsetAsync(numP, 0, (size_t)B * 8, s));
+  CK(cudaMemsetAsync(denP, 0, (size_t)B * 8, s));
+  CK(cudaMemsetAsync(aw, 0, (size_t)nO * 4, s));
+  CK(cudaMemsetAsync(AT, 0, (size_t)NP * 4, s));
+  ptycho::PosArgs F2 = F;
+  F2.lpart = partials + B;  // the loss of this pass is not used
+  ProblemDesc d2 = base_desc(c, L, O, pos_all, idx, B, n_pos);
+  d2.gO = c->gO;
+  d2.lsq_dO = dO;
+  d2.lsq_dPhat = dPhat;
+  d2.lsq_num = num;
+  d2.lsq_den = den;
+  d2.lsq_numP = numP;
+  d2.lsq_denP = denP;
+  d2.lsq_aw = aw;
+  LaunchArgs la2 = one_problem(c, L, d2);
+  la2.slot_stride = stride;
+  CK(cudaMemsetAsync(F2.lpart, 0, (size_t)B * 8, s));
+  {
+    Timed t(c, "adjoint", s);
+    CK(c->ops->adjoint_pos(la2, F2, clusters, ptycho::kVarLsqStep, s));
+  }
+  {
+    Timed t(c, "lsq_update", s);
+    CK(ptycho::launch_transmission(reinterpret_cast<const float2*>(O), S, c->g.H, c->g.W, c->N, pos_all, idx, n_pos, B,
+                                   numP, denP, opt->gamma, AT, s));
+    CK(ptycho::launch_weighted_update(reinterpret_cast<float2*>(O), dO, aw, il, opt->beta_O, nO, nO, s));
+    CK(ptycho::launch_weighted_update(reinterpret_cast<float2*>(P), dP, AT, T, opt->beta_P, (long long)K * NP, NP, s));
+  }
   return PTYCHO_OK;
 }
 

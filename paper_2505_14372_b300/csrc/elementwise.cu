@@ -233,6 +233,99 @@ cudaError_t launch_axpy(float2* z, const float2* g, long long n, float a, cudaSt
   return cudaGetLastError();
 }
 
+// LSQML (§3.3.2) helpers.
+// Transmission prod_s |O_s|^2 of every position's window, summed into the
+// probe frame T[N][N]; with step sums, weighted by the position's probe step
+// num[j] / (den[j] + gamma).  Positions outside [0, npos) or the object add
+// nothing.
+__global__ void k_transmission(const float2* __restrict__ O, int S, int H, int W, int N, const float* __restrict__ pos,
+                               const int* __restrict__ idx, int npos, int B, const double* __restrict__ num,
+                               const double* __restrict__ den, float gamma, float* __restrict__ T) {
+  const long long NP = (long long)N * N, total = (long long)B * NP;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / NP);
+    const int p = (int)(e - (long long)j * NP);
+    const int jj = idx ? idx[j] : j;
+    if (jj < 0 || jj >= npos) continue;
+    const double fy = floor((double)pos[2 * (size_t)jj] + 0.5), fx = floor((double)pos[2 * (size_t)jj + 1] + 0.5);
+    if (!(fy >= 0.0 && fx >= 0.0 && fy + N <= (double)H && fx + N <= (double)W)) continue;
+    const int r = p / N, c = p - r * N;
+    const float2* o = O + ((size_t)fy + r) * W + (size_t)fx + c;
+    float t = 1.f;
+    for (int s = 0; s < S; ++s) t *= cabs2(__ldg(o + (size_t)s * H * W));
+    float wgt = 1.f;
+    if (num) {
+      const double d = den[j] + (double)gamma;
+      wgt = d > 0.0 ? (float)(num[j] / d) : 0.f;
+    }
+    atomicAdd(T + p, wgt * t);
+  }
+}
+
+// out[e] = num[e] / (den[e % period] + reg), 0 where that is not positive
+// (den = den_prev when given)
+__global__ void k_divide(const float2* __restrict__ num, const float* __restrict__ den, const float* __restrict__ den_prev,
+                         float reg, long long n, long long period, float2* __restrict__ out) {
+  const float* d = den_prev ? den_prev : den;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float q = __ldg(d + e % period) + reg;
+    const float2 v = __ldg(num + e);
+    out[e] = q > 0.f ? make_float2(v.x / q, v.y / q) : make_float2(0.f, 0.f);
+  }
+}
+
+// z[e] += beta dz[e] aw[e % period] / w[e % period] (unchanged where w = 0)
+__global__ void k_weighted_update(float2* __restrict__ z, const float2* __restrict__ dz, const float* __restrict__ aw,
+                                  const float* __restrict__ w, float beta, long long n, long long period) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long q = e % period;
+    const float ww = __ldg(w + q);
+    if (!(ww > 0.f)) continue;
+    const float f = beta * __ldg(aw + q) / ww;
+    const float2 d = __ldg(dz + e);
+    float2 v = z[e];
+    v.x = fmaf(f, d.x, v.x);
+    v.y = fmaf(f, d.y, v.y);
+    z[e] = v;
+  }
+}
+
+// y[e] += x[e] (float)
+__global__ void k_add(float* __restrict__ y, const float* __restrict__ x, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] += __ldg(x + e);
+}
+
+static int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 148LL * 16)); }
+
+cudaError_t launch_transmission(const float2* O, int S, int H, int W, int N, const float* pos, const int* idx, int npos,
+                                int B, const double* num, const double* den, float gamma, float* T, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  count_launch();
+  k_transmission<<<grid_for((long long)B * N * N), 256, 0, s>>>(O, S, H, W, N, pos, idx, npos, B, num, den, gamma, T);
+  return cudaGetLastError();
+}
+cudaError_t launch_divide(const float2* num, const float* den, const float* den_prev, float reg, long long n,
+                          long long period, float2* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  k_divide<<<grid_for(n), 256, 0, s>>>(num, den, den_prev, reg, n, period, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_weighted_update(float2* z, const float2* dz, const float* aw, const float* w, float beta, long long n,
+                                   long long period, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  k_weighted_update<<<grid_for(n), 256, 0, s>>>(z, dz, aw, w, beta, n, period);
+  return cudaGetLastError();
+}
+cudaError_t launch_add(float* y, const float* x, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  k_add<<<grid_for(n), 256, 0, s>>>(y, x, n);
+  return cudaGetLastError();
+}
+
 }  // namespace ptycho
 
 extern "C" uint64_t ptycho_kernels_launched(void) { return ptycho::launches_so_far(); }

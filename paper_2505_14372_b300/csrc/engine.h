@@ -61,6 +61,13 @@ cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long lo
                         float b2, float eps, float bc1, float bc2, cudaStream_t s);
 cudaError_t launch_slice_absmax(const float2* O, int S, long long per_slice, unsigned* omax, cudaStream_t s);
 cudaError_t launch_axpy(float2* z, const float2* g, long long n, float a, cudaStream_t s);
+cudaError_t launch_transmission(const float2* O, int S, int H, int W, int N, const float* pos, const int* idx, int npos,
+                                int B, const double* num, const double* den, float gamma, float* T, cudaStream_t s);
+cudaError_t launch_divide(const float2* num, const float* den, const float* den_prev, float reg, long long n,
+                          long long period, float2* out, cudaStream_t s);
+cudaError_t launch_weighted_update(float2* z, const float2* dz, const float* aw, const float* w, float beta, long long n,
+                                   long long period, cudaStream_t s);
+cudaError_t launch_add(float* y, const float* x, long long n, cudaStream_t s);
 
 // process-wide count of kernels this library has launched (engine_impl /
 // elementwise launchers bump it once per launch)

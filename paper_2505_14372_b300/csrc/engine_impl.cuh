@@ -12,8 +12,9 @@ namespace ptycho {
 // ALLV: instantiate every Variant (otherwise FP32 gradient kernels only).
 template <class TL, bool ALLV = true>
 struct Engine {
-  // calls f(std::integral_constant<int, V>) for the runtime variant
-  template <class F>
+  // calls f(std::integral_constant<int, V>) for the runtime variant; the
+  // LSQML passes exist only for the position-major kernel (MAXV)
+  template <int MAXV = kVarEpie, class F>
   static cudaError_t with_variant(int variant, const F& f) {
     if constexpr (ALLV) {
       switch (variant) {
@@ -21,6 +22,12 @@ struct Engine {
         case kVarF16: return f(std::integral_constant<int, kVarF16>{});
         case kVarBF16: return f(std::integral_constant<int, kVarBF16>{});
         case kVarEpie: return f(std::integral_constant<int, kVarEpie>{});
+        case kVarLsqDir:
+          if constexpr (MAXV >= kVarLsqDir) return f(std::integral_constant<int, kVarLsqDir>{});
+          else return cudaErrorNotSupported;
+        case kVarLsqStep:
+          if constexpr (MAXV >= kVarLsqStep) return f(std::integral_constant<int, kVarLsqStep>{});
+          else return cudaErrorNotSupported;
         default: return cudaErrorNotSupported;
       }
     } else {
@@ -128,12 +135,12 @@ struct Engine {
     return cudaGetLastError();
   }
   static cudaError_t adjoint_pos(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s) {
-    return with_variant(variant,
-                        [&](auto v) { return launch(k_adjoint_pos<TL, decltype(v)::value>, clusters, s, L, F); });
+    return with_variant<kVarLsqStep>(
+        variant, [&](auto v) { return launch(k_adjoint_pos<TL, decltype(v)::value>, clusters, s, L, F); });
   }
   static int resident_pos(int variant) {
     int n = 0;
-    with_variant(variant, [&](auto v) {
+    with_variant<kVarLsqStep>(variant, [&](auto v) {
       n = resident(k_adjoint_pos<TL, decltype(v)::value>);
       return cudaSuccess;
     });

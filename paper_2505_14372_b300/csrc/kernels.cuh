@@ -53,10 +53,25 @@ __device__ __forceinline__ float2 wave_get(const char* base, int i) {
 // Compile-time properties of a kernel variant (launch.h: Variant).
 template <int V>
 struct Var {
-  static constexpr int prec = V == kVarEpie ? 0 : V;  // entry-wave storage format
+  static constexpr int prec = V <= kVarBF16 ? V : 0;  // entry-wave storage format
   static constexpr bool epie = V == kVarEpie;         // ePIE normalisers (§3.3.1)
+  static constexpr bool lsq_dir = V == kVarLsqDir;    // LSQML direction pass (§3.3.2)
+  static constexpr bool lsq_step = V == kVarLsqStep;  // LSQML step-size pass
   static constexpr size_t wave_bytes = prec ? 4 : 8;
+  // entry waves per mode in a slot: S, plus the shifted probe direction in
+  // the step pass
+  static constexpr int extra_waves = lsq_step ? 1 : 0;
 };
+
+__device__ __forceinline__ void red_add1(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 __device__ __forceinline__ const ProblemDesc& find_desc(const LaunchArgs& L, int item) {
   int d = 0;
@@ -206,10 +221,12 @@ __device__ void forward_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
     const int W = D.W;
     // row s1' (finishing psi_s) -> store psi_s -> transmit -> row s1
     float lm = 0.f;
+    float* ils = Var<V>::lsq_dir ? D.lsq_il + (size_t)s * D.H * D.W + (size_t)g.ny * D.W + g.nx : nullptr;
     TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, PreO{Os, W},
                                          [&](int r, int c, float2& v, const float2& o) {
                                            if constexpr (WAVES) wave_put<PREC>(wv, r * N + c, v);
                                            if constexpr (WMAX) lm = fmaxf(lm, cabs2(v));
+                                           if constexpr (Var<V>::lsq_dir) red_add1(ils + (size_t)r * W + c, cabs2(v));
                                            v = cmul(v, o);
                                          });
     if constexpr (WMAX) {
@@ -246,7 +263,40 @@ __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
     const char* wv = waves + (size_t)s * TL::NP * Var<V>::wave_bytes;
     const int W = D.W;
     // row s1' (finishing g_phi_s) -> object gradient, g_psi_s = conj(O) g_phi -> row s1
-    if constexpr (Var<V>::epie) {
+    if constexpr (Var<V>::lsq_step) {
+      // LSQML step sizes: with chi_s = g_phi_s (the exit-plane update) and
+      // q = dO_s psi_s, sum Re(chi conj q) and |q|^2 over the window; at the
+      // entry slice also with q = O_0 S_j dP_k (the shifted probe direction,
+      // kept after this mode's entry waves)
+      const float2* dOs = D.lsq_dO + ooff;
+      const float2* sdp = reinterpret_cast<const float2*>(waves + (size_t)D.S * TL::NP * Var<V>::wave_bytes);
+      float num = 0.f, den = 0.f, nump = 0.f, denp = 0.f;
+      TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, PrePsiO<0>{wv, N, Os, W},
+                                           [&](int r, int c, float2& v, const PsiO& p) {
+                                             const float2 q = cmul(__ldg(dOs + (size_t)r * W + c), p.psi);
+                                             num = fmaf(v.x, q.x, fmaf(v.y, q.y, num));
+                                             den += cabs2(q);
+                                             if (s == 0) {
+                                               const float2 qp = cmul(p.o, sdp[r * N + c]);
+                                               nump = fmaf(v.x, qp.x, fmaf(v.y, qp.y, nump));
+                                               denp += cabs2(qp);
+                                             }
+                                             v = cconjmul(p.o, v);
+                                           });
+      const double sn = warp_sum((double)num), sd = warp_sum((double)den);
+      if ((threadIdx.x & 31) == 0) {
+        atomicAdd(D.lsq_num + (size_t)g.j * D.S + s, sn);
+        atomicAdd(D.lsq_den + (size_t)g.j * D.S + s, sd);
+      }
+      if (s == 0) {
+        const double pn = warp_sum((double)nump), pd = warp_sum((double)denp);
+        if ((threadIdx.x & 31) == 0) {
+          atomicAdd(D.lsq_numP + g.j, pn);
+          atomicAdd(D.lsq_denP + g.j, pd);
+        }
+        break;  // nothing further of the chain is needed
+      }
+    } else if constexpr (Var<V>::epie) {
       const float inv_o = 1.0f / fmaxf(__uint_as_float(__ldg(D.omax + s)), FLT_MIN);
       const float inv_p =
           1.0f / fmaxf(__uint_as_float(__ldcg(D.wmax + ((size_t)g.j * D.K + g.k) * D.S + s)), FLT_MIN);
@@ -421,7 +471,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
   const int K = D.K;
   const int cid = cluster_id<TL>();
   char* slot = L.slots + (size_t)cid * L.slot_stride;
-  const size_t wstride = (size_t)D.S * TL::NP * Var<V>::wave_bytes;  // one mode's entry waves
+  // one mode's entry waves (and, in the LSQML step pass, its shifted probe direction)
+  const size_t wstride = (size_t)(D.S + Var<V>::extra_waves) * TL::NP * Var<V>::wave_bytes;
   float2* Ab = F.Abuf + (size_t)cid * K * TL::NP;
   float* Ib = F.Ibuf + (size_t)cid * TL::NP;
 #pragma unroll 1
@@ -440,6 +491,22 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
     for (int k = 0; k < K; ++k) {
       if (k) TL::sync_cluster();
       g.k = k;
+      if constexpr (Var<V>::lsq_step) {
+        // S_j dP_k = F^-1[ramp . F dP_k], natural order, after the mode's entry waves
+        float2* out = reinterpret_cast<float2*>(slot + k * wstride + (size_t)D.S * TL::NP * Var<V>::wave_bytes);
+        const float2* dPh = D.lsq_dPhat + (size_t)k * TL::NP;
+        const float2* rY = sm.rampY;
+        const float2* rX = sm.rampX;
+        TL::template col_contig<false, false, true>(
+            sm.wave, sm.twC, rank,
+            [&](int pu, int pv) { return cscale(cmul(cmul(__ldg(dPh + pu * N + pv), rY[pu]), rX[pv]), inv); },
+            NoOp{});
+        __syncthreads();
+        TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+        TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{}, NoPre{},
+                                              [&](int r, int c, float2& v, const NoPre::type&) { out[r * N + c] = v; });
+        TL::sync_cluster();
+      }
       forward_chain<TL, V, true>(sm, rank, D, g, slot + k * wstride);
       float2* Ak = Ab + (size_t)k * TL::NP;
       const bool first = k == 0, last = k + 1 == K;
@@ -479,6 +546,25 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
       __syncthreads();
       TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
       adjoint_chain<TL, V>(sm, rank, D, g, slot + k * wstride);
+    }
+    if constexpr (Var<V>::lsq_step) {
+      // every mode has added its sums: step-weighted illumination
+      // alpha_{s,j} sum_k |psi_{s,k}|^2 over this CTA's rows of the window
+      TL::sync_cluster();
+      const int W = D.W;
+#pragma unroll 1
+      for (int s = 0; s < D.S; ++s) {
+        const double num = __ldcg(D.lsq_num + (size_t)j * D.S + s), den = __ldcg(D.lsq_den + (size_t)j * D.S + s);
+        const float a = den + (double)F.gamma > 0.0 ? (float)(num / (den + (double)F.gamma)) : 0.f;
+        float* aws = D.lsq_aw + (size_t)s * D.H * D.W + (size_t)g.ny * D.W + g.nx;
+        for (int e = threadIdx.x; e < TL::ROWS * N; e += TL::T) {
+          const int r = rank * TL::ROWS + e / N, c = e % N;
+          float w = 0.f;
+          for (int k = 0; k < K; ++k)
+            w += cabs2(__ldcg(reinterpret_cast<const float2*>(slot + k * wstride + (size_t)s * TL::NP * 8) + r * N + c));
+          red_add1(aws + (size_t)r * W + c, a * w);
+        }
+      }
     }
   }
   // no CTA leaves while its partner may still be sending to it

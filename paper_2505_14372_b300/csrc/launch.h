@@ -12,7 +12,12 @@ constexpr int kModelEpie = 3;                      // noise-model id of the ePIE
 // Kernel variants of the forward / adjoint kernels: the storage format of
 // the entry-wave copies (FP32, binary16, bfloat16) and the ePIE normalisers
 // are compile-time properties of their real-space stages.
-enum Variant { kVarF32 = 0, kVarF16 = 1, kVarBF16 = 2, kVarEpie = 3 };
+// LSQML (§3.3.2) runs two passes: kVarLsqDir accumulates the update
+// directions (the plain adjoint chain from the modulus-update seed) and the
+// group's illumination; kVarLsqStep recomputes the chain and reduces the
+// per-position least-squares step sizes, then scatters the step-weighted
+// illumination.
+enum Variant { kVarF32 = 0, kVarF16 = 1, kVarBF16 = 2, kVarEpie = 3, kVarLsqDir = 4, kVarLsqStep = 5 };
 
 // One problem (dataset) inside a launch.  All pointers are device pointers.
 struct ProblemDesc {
@@ -35,6 +40,18 @@ struct ProblemDesc {
   // per item and slice [B][K][S], both as float bits (atomicMax)
   const unsigned* omax;
   unsigned* wmax;
+  // LSQML (null otherwise): illumination [S][H][W] (direction pass), object
+  // direction [S][H][W] and probe-direction spectra [K][NP] (slot order),
+  // step-size sums per position and slice [B][S] and per position [B], and
+  // the step-weighted illumination [S][H][W] (step pass)
+  float* lsq_il;
+  const float2* lsq_dO;
+  const float2* lsq_dPhat;
+  double* lsq_num;
+  double* lsq_den;
+  double* lsq_numP;
+  double* lsq_denP;
+  float* lsq_aw;
 };
 
 struct LaunchArgs {
@@ -57,6 +74,7 @@ struct PosArgs {
   double* lpart;       // [B] loss per position (zeroed per launch)
   int model;           // noise model
   float eps, c;
+  float gamma;         // LSQML step-size regulariser
 };
 
 }  // namespace ptycho
