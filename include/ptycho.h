@@ -293,6 +293,14 @@ int ptycho_make_groups(int32_t P, int32_t B, uint64_t seed, int64_t iteration, i
 int ptycho_set_timing(ptycho_ctx* ctx, int32_t enable);
 int ptycho_kernel_times(ptycho_ctx* ctx, const char** names, double* ms, int32_t* launches, int32_t cap);
 
+/* Self-test of failure detection on the device (N = 192, the tile whose
+ * layout switches wait on mbarriers): launches one cluster whose exchange
+ * waits for data that nothing sends, with a short poll limit, so every wait
+ * gives up, flags the time-out and returns (no hang, no fault).  Returns
+ * PTYCHO_ETIMEDOUT when the flag was seen, as expected; PTYCHO_OK would
+ * mean the wait did not give up.  Synchronises the device. */
+int ptycho_exchange_selftest(int32_t N);
+
 /* Stand-alone 2-D DFT of `count` natural-order N x N complex64 arrays
  * through the same shared-memory tile the model uses (dir < 0 forward,
  * dir > 0 inverse, both unnormalised).  For tests and diagnostics. */

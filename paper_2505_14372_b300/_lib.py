@@ -88,6 +88,7 @@ SIGNATURES = {
                                C.POINTER(C.c_double), C.POINTER(C.c_double), P_]),
     "ptycho_epie_step": (I32, [P_, P_, P_, C.c_float, C.c_float, P_, P_, I32, P_, I32, P_, P_]),
     "ptycho_lsqml_step": (I32, [P_, P_, P_, C.POINTER(LsqmlOpt), P_, P_, P_, P_, P_, P_, I32, P_, I32, P_, P_]),
+    "ptycho_exchange_selftest": (I32, [I32]),
     "ptycho_check": (I32, [P_, P_]),
     "ptycho_make_groups": (I32, [I32, I32, C.c_uint64, C.c_int64, I32, P_, P_]),
     "ptycho_set_timing": (I32, [P_, I32]),

@@ -833,6 +833,18 @@ int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, i
   return PTYCHO_OK;
 }
 
+int ptycho_exchange_selftest(int32_t N) {
+  const EngineOps* ops = ptycho::engine_for(N);
+  if (!ops) return perr(PTYCHO_EINVAL, "N not in {64, 128, 192, 256}");
+  if (ops->G != 2) return perr(PTYCHO_EINVAL, "only the 192 x 192 tile exchanges through mbarriers");
+  ops->take_exchange_timeouts();  // clear
+  CK(ops->exchange_probe(nullptr));
+  CK(cudaDeviceSynchronize());
+  if (ops->take_exchange_timeouts())
+    return perr(PTYCHO_ETIMEDOUT, "the exchange wait gave up as the self-test expects");
+  return PTYCHO_OK;
+}
+
 const char* ptycho_version(void) { return "libptycho 0.1 (sm_103a)"; }
 
 }  // extern "C"

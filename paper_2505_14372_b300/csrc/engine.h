@@ -28,6 +28,8 @@ struct EngineOps {
   // bounded exchange waits of this tile's kernels that gave up since the
   // last call (read and cleared)
   unsigned (*take_exchange_timeouts)();
+  // launches the bounded-wait self-test (one cluster whose waits run out)
+  cudaError_t (*exchange_probe)(cudaStream_t s);
   bool has_variants;  // reduced-precision waves and ePIE are instantiated
 };
 

@@ -157,6 +157,9 @@ struct Engine {
     return n;
   }
 
+  // one cluster of the bounded-wait self-test kernel
+  static cudaError_t exchange_probe(cudaStream_t s) { return launch(k_exchange_timeout_probe<TL>, 1, s); }
+
   static unsigned take_exchange_timeouts() {
     unsigned v = 0;
     if (cudaMemcpyFromSymbol(&v, g_exchange_timeouts, sizeof(v)) != cudaSuccess) {
@@ -174,7 +177,7 @@ struct Engine {
     static const EngineOps o = {TL::N,         TL::G,      TL::T,       TL::R1,      TL::R2,
                                 TL::SMEM,      &probe_spectrum, &forward, &adjoint,  &probe_grad,
                                 &fft_debug,    &modesum,   &loss,       &seed,       &resident_clusters,
-                                &adjoint_pos,  &resident_pos, &take_exchange_timeouts, ALLV};
+                                &adjoint_pos,  &resident_pos, &take_exchange_timeouts, &exchange_probe, ALLV};
     return &o;
   }
 };

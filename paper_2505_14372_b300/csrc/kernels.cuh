@@ -625,6 +625,19 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_grad(const float2* __
   TL::sync_cluster();
 }
 
+// Self-test of the exchange's bounded wait (tests): every CTA of one cluster
+// waits for a block that nothing sends, with a short poll limit, so each
+// wait gives up and flags the time-out; the CTAs then leave together.
+template <class TL>
+__global__ void __launch_bounds__(TL::T, TL::MINB) k_exchange_timeout_probe() {
+  extern __shared__ float4 smem_raw[];
+  Smem<TL> sm(smem_raw);
+  TL::init_tables(sm.twS, sm.twC, sm.fsq);
+  TL::sync_cluster();
+  if constexpr (TL::XB) TL::exchange_wait(sm.wave, 0, 1u << 12);
+  TL::sync_cluster();
+}
+
 // Stand-alone 2-D DFT of natural-order arrays through the tile (tests).
 // dir < 0: unnormalised forward; dir > 0: unnormalised inverse.
 template <class TL>

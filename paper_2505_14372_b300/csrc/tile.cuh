@@ -216,14 +216,14 @@ struct Tile {
   // Waits until the partner's block for this layout switch has arrived
   // (bounded: gives up after kExchangeSpin polls and flags it), then makes
   // this CTA's own writes of the stage visible to all its threads.
-  __device__ static void exchange_wait(const float2* wave, int which) {
+  __device__ static void exchange_wait(const float2* wave, int which, unsigned spin_limit = kExchangeSpin) {
     const uint32_t bar = bar_addr(wave, which);
     uint64_t tok = 0;
     if ((threadIdx.x & 31) == 0) tok = threadIdx.x == 0 ? mbar_arrive_tx(bar, BLK * 8) : mbar_arrive(bar);
     tok = __shfl_sync(0xffffffffu, tok, 0);
     unsigned it = 0;
     while (!mbar_try_wait(bar, tok)) {
-      if (++it > kExchangeSpin) {
+      if (++it > spin_limit) {
         atomicOr(&g_exchange_timeouts, 1u);
         break;
       }
