@@ -545,7 +545,7 @@ def main():
     if os.path.exists(traffic_path):
         with open(traffic_path) as f:
             tj = json.load(f)
-        key = f"{dom}/{args.workload}/{args.waves}/{args.wave_prec}"
+        key = f"{dom}/{args.workload}/{args.waves}/{args.wave_prec}" + ("" if args.engine == "gd" else "/" + args.engine)
         # counters are only valid for the kernel source they were taken on
         if key in tj and tj[key].get("kernel_source") == kernel_source_hash():
             traffic = tj[key]["bytes_per_item"] * B * wl.K
