@@ -22,20 +22,24 @@
 // is a block transpose across the cluster: element (CTA c, block b, row r,
 // column cc) moves to (CTA b, block c, r, cc); it is fused into the last
 // stage of a row pass (row -> column) and of an inverse column pass (column
-// -> row).  For G = 2 the off-diagonal block goes with st.async into the
-// partner's idle buffer and is counted on the partner's mbarrier (no cluster
-// barrier per switch); G = 4 stages it in registers and writes it with
+// -> row).  For G = 2 that stage writes its results in place and the
+// off-diagonal block (the same swizzle in both CTAs) goes to the partner's
+// idle buffer as bulk shared::cluster copies, one per finished round of
+// tasks, so the transfer overlaps the remaining rounds; the copies count
+// their bytes on the partner's mbarrier (no cluster barrier per switch).
+// G = 4 stages the block in registers and writes it with
 // st.shared::cluster between two cluster barriers.
 //
-// Bank conflicts: slot (b, r, cc) sits at b*ROWS^2 + r*ROWS +
-// 2((cc >> 1) ^ f) + (cc & 1) with f = (R1 r + NB b + cc / R2) mod 8,
-// NB = ROWS / R2: the XOR permutes 16-byte column pairs, so columns cc, cc+1
-// (cc even) stay adjacent and in order.  The strided and column stages walk
-// 16 consecutive cc of one row with 8-byte accesses (f constant: 16
-// distinct bank pairs per half-warp); the row-contiguous stage reads and
-// writes its 16 consecutive columns as 8 16-byte pairs, and its lanes
-// (r, k1) have f = (R1 r + k1) mod 8 = lane id mod 8, so each quarter-warp
-// hits 8 distinct 16-byte bank groups.
+// Bank conflicts: slot (b, r, cc) sits at base(b) + r*ROWS +
+// 2((cc >> 1) ^ f) + (cc & 1) with f = (R1 r + cc / R2 + o) mod 8: the XOR
+// permutes 16-byte column pairs, so columns cc, cc+1 (cc even) stay adjacent
+// and in order.  o = NB b (NB = ROWS / R2) for G = 1, 4; for G = 2, o = 6 on
+// the off-diagonal block and 4 * rank on the diagonal one.  The strided and
+// column stages walk 16 consecutive cc of one row with 8-byte accesses (f
+// constant: 16 distinct bank pairs per half-warp); the row-contiguous stage
+// reads and writes its 16 consecutive columns as 8 16-byte pairs, and the 8
+// lanes (r, k1) of a quarter-warp (a run of 8 consecutive k1 mod R1) get 8
+// distinct f, so they hit 8 distinct 16-byte bank groups.
 #pragma once
 #include <stdint.h>
 
@@ -77,14 +81,14 @@ __device__ __forceinline__ void red_add(float2* p, float2 v) {
 }
 
 // ---- mbarrier-signalled exchange between the two CTAs of a 192x192 tile --
-// A layout switch writes the off-diagonal block straight into the partner's
-// idle buffer with st.async, each store counting its bytes on the partner's
-// mbarrier; the partner waits on that mbarrier (expected bytes = one block)
-// instead of both CTAs meeting at a cluster barrier.  No release fence is
-// needed on the sending side.  Reuse of a buffer is ordered by the data
-// flow: a CTA writes its partner's buffer only after it has received the
-// partner's data of the opposite switch, which the partner sends after its
-// last read of that buffer.
+// A layout switch copies the off-diagonal block into the partner's idle
+// buffer with bulk copies that count their bytes on the partner's mbarrier;
+// the partner waits on that mbarrier (expected bytes = one block) instead of
+// both CTAs meeting at a cluster barrier.  Reuse of a buffer is ordered by
+// the data flow: a CTA copies into its partner's buffer only after it has
+// received the partner's data of the opposite switch, which the partner
+// sends (from that very buffer) after its last write to it, and whose
+// arrival means the copy engine has finished reading it.
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -106,16 +110,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint64_t st) {
       : "r"(bar), "l"(st)
       : "memory");
   return ok != 0;
-}
-__device__ __forceinline__ void st_async(uint32_t addr, float2 v, uint32_t remote_bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
-               "f"(v.x), "f"(v.y), "r"(remote_bar)
-               : "memory");
-}
-__device__ __forceinline__ void st_async2(uint32_t addr, float2 a, float2 b, uint32_t remote_bar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
-               "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "r"(remote_bar)
-               : "memory");
 }
 __device__ __forceinline__ void st_cluster2(uint32_t addr, float2 a, float2 b) {
   asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a.x), "f"(a.y), "f"(b.x),
@@ -178,11 +172,17 @@ struct Tile {
   // the row layout (COL = false) or the column layout (COL = true)
   template <bool COL>
   __device__ static __forceinline__ int slot(int rank, int b, int r, int cc) {
-    const int f = (R1 * r + NB * b + cc / R2) & 7;
-    int base;
-    if constexpr (G == 1) base = 0;
-    else if constexpr (XB) base = b == rank ? 0 : (COL ? 2 * BLK : BLK);
-    else base = b * BLK;
+    int base, f;
+    if constexpr (XB) {
+      // the off-diagonal block has the same swizzle in both CTAs and both
+      // layouts, so a layout switch moves it as one contiguous bulk copy
+      const bool diag = b == rank;
+      base = diag ? 0 : (COL ? 2 * BLK : BLK);
+      f = (R1 * r + cc / R2 + (diag ? 4 * rank : 6)) & 7;
+    } else {
+      base = G == 1 ? 0 : b * BLK;
+      f = (R1 * r + NB * b + cc / R2) & 7;
+    }
     return base + r * ROWS + (((cc >> 1) ^ f) << 1) + (cc & 1);
   }
   // 16-byte pair (slots s, s + 1) holding columns cc, cc + 1 (cc even)
@@ -230,6 +230,32 @@ struct Tile {
     }
     __syncthreads();
   }
+
+  // Layout switch of the 2-CTA tile: the stage writes its results in place
+  // and sends its off-diagonal block to the partner's idle buffer as bulk
+  // copies (one per finished round of tasks where the rounds cover whole
+  // row ranges) that count their bytes on the partner's mbarrier `which`.
+  // publish() makes every thread's shared-memory writes visible to the copy
+  // engine; push() sends slots [s0, s0 + n) of block `src` to the same slots
+  // of the partner's block `dst`.
+  __device__ static void publish() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+  }
+  __device__ static void push(float2* wave, int rank, int src, int dst, int which, int s0, int n) {
+    const uint32_t peer = (uint32_t)(rank ^ 1);
+    const uint32_t from = smem_u32(wave + (size_t)src * BLK + s0);
+    const uint32_t to = cluster_map(smem_u32(wave + (size_t)dst * BLK + s0), peer);
+    const uint32_t bar = cluster_map(bar_addr(wave, which), peer);
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(to),
+                 "r"(from), "r"((uint32_t)n * (uint32_t)sizeof(float2)), "r"(bar)
+                 : "memory");
+  }
+  // row -> column: a round of the row-contiguous stage finishes T / R1 whole
+  // rows; column -> row: a round of the column-strided stage finishes T /
+  // ROWS consecutive n2, i.e. NB runs of T / ROWS rows of the block
+  static constexpr bool ROW_ROUNDS = XB && T % R1 == 0 && TC % T == 0;
+  static constexpr bool COL_ROUNDS = XB && T % ROWS == 0 && TS % T == 0;
 
   __device__ static void init_tables(float2* twS, float2* twC, int* fsq) {
     if constexpr (XB) {
@@ -351,7 +377,6 @@ struct Tile {
       cluster_arrive_release();
       cluster_wait();
     } else {
-      const uint32_t w0 = smem_u32(wave);
       // when T is a multiple of R1 every task of a thread has the same k1, so
       // the inverse stage's twiddles are loaded once per stage
       constexpr bool HOIST = DIR > 0 && (T % R1 == 0);
@@ -377,20 +402,21 @@ struct Tile {
             else x[i] = cmulc(x[i], twC[i * R1 + k1]);
           }
         }
-        if (DIR > 0 || G == 1 || b == rank) {
-          // in place (row layout) or the diagonal block (same slots in both layouts)
+        // in place: the diagonal block has the same slots in both layouts,
+        // the off-diagonal one goes to the partner's column-layout buffer
 #pragma unroll
-          for (int m = 0; m < R2; m += 2) st_pair(wave, rslot(rank, b, r, cc0 + m), x[m], x[m + 1]);
-        } else {
-          // off-diagonal block -> the partner's idle column-layout buffer
-          const uint32_t base = cluster_map(w0, (uint32_t)b);
-          const uint32_t rbar = cluster_map(bar_addr(wave, 1), (uint32_t)b);
-#pragma unroll
-          for (int m = 0; m < R2; m += 2)
-            st_async2(base + 8u * (uint32_t)cslot(b, rank, r, cc0 + m), x[m], x[m + 1], rbar);
+        for (int m = 0; m < R2; m += 2) st_pair(wave, rslot(rank, b, r, cc0 + m), x[m], x[m + 1]);
+        if constexpr (DIR < 0 && ROW_ROUNDS) {
+          constexpr int RR = T / R1;  // rows finished per round
+          publish();
+          if (threadIdx.x == 0) push(wave, rank, 1, 2, 1, t * RR * ROWS, RR * ROWS);
         }
       }
       if constexpr (DIR < 0 && G > 1) {
+        if constexpr (!ROW_ROUNDS) {
+          publish();
+          if (threadIdx.x == 0) push(wave, rank, 1, 2, 1, 0, BLK);
+        }
         exchange_wait(wave, 1);
       } else {
         __syncthreads();
@@ -436,15 +462,6 @@ struct Tile {
       cluster_arrive_release();
       cluster_wait();
     } else {
-      const uint32_t w0 = smem_u32(wave);
-      uint32_t base[G], rbar[G];
-      if constexpr (DIR > 0 && XB) {
-#pragma unroll
-        for (int b = 0; b < G; ++b) {
-          base[b] = cluster_map(w0, (uint32_t)b);
-          rbar[b] = cluster_map(bar_addr(wave, 0), (uint32_t)b);
-        }
-      }
 #pragma unroll 1
       for (int t = 0; t < SPT; ++t) {
         const int id = threadIdx.x + t * T;
@@ -461,15 +478,22 @@ struct Tile {
           for (int i = 0; i < R1; ++i) wave[cslot(rank, i / NB, n2 + R2 * (i % NB), cc)] = x[i];
         } else {
           Dft<R1, +1>::run(x);
+          // in place (the diagonal block has the same slots in both layouts;
+          // the off-diagonal one goes to the partner's row-layout buffer)
 #pragma unroll
-          for (int i = 0; i < R1; ++i) {
-            const int b = i / NB, r = n2 + R2 * (i % NB);
-            if (G == 1 || b == rank) wave[rslot(rank, b, r, cc)] = x[i];
-            else st_async(base[b] + 8u * (uint32_t)rslot(b, rank, r, cc), x[i], rbar[b]);  // partner's idle buffer
+          for (int i = 0; i < R1; ++i) wave[cslot(rank, i / NB, n2 + R2 * (i % NB), cc)] = x[i];
+          if constexpr (G > 1 && COL_ROUNDS) {
+            constexpr int RN = T / ROWS;  // consecutive n2 finished per round
+            publish();
+            if ((int)threadIdx.x < NB) push(wave, rank, 2, 1, 0, (RN * t + R2 * (int)threadIdx.x) * ROWS, RN * ROWS);
           }
         }
       }
       if constexpr (DIR > 0 && G > 1) {
+        if constexpr (!COL_ROUNDS) {
+          publish();
+          if (threadIdx.x == 0) push(wave, rank, 2, 1, 0, 0, BLK);
+        }
         exchange_wait(wave, 0);
       } else {
         __syncthreads();
