@@ -161,6 +161,8 @@ struct Tile {
   static_assert(N == R1 * R2 && R2 % 16 == 0, "N = R1 R2 with R2 a multiple of 16");
   static_assert(N % G == 0 && ROWS % R2 == 0 && ROWS % 16 == 0, "block split");
   static_assert(T % 32 == 0, "whole warps");
+  static_assert(!XB || (TC % T == 0 && TS % T == 0 && ROWS % 32 == 0 && NB * 2 == R1),
+                "2-CTA exchange: whole rounds, warps of 32 consecutive columns");
 
   // natural DFT bin held by spectral slot p, and slot of natural bin n
   __host__ __device__ static constexpr int nat(int p) { return p / R2 + R1 * (p % R2); }
@@ -232,16 +234,13 @@ struct Tile {
   }
 
   // Layout switch of the 2-CTA tile: the stage writes its results in place
-  // and sends its off-diagonal block to the partner's idle buffer as bulk
-  // copies (one per finished round of tasks where the rounds cover whole
-  // row ranges) that count their bytes on the partner's mbarrier `which`.
-  // publish() makes every thread's shared-memory writes visible to the copy
-  // engine; push() sends slots [s0, s0 + n) of block `src` to the same slots
-  // of the partner's block `dst`.
-  __device__ static void publish() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-  }
+  // and every warp sends the off-diagonal slots it has just finished to the
+  // same slots of the partner's idle buffer as bulk shared::cluster copies
+  // that count their bytes on the partner's mbarrier `which`, so the
+  // transfer overlaps the rest of the stage.  push() copies slots
+  // [s0, s0 + n) of block `src` to block `dst` of the partner; the caller has
+  // made the slots' writes visible to the copy engine (fence.proxy.async by
+  // the writing threads, then a warp barrier).
   __device__ static void push(float2* wave, int rank, int src, int dst, int which, int s0, int n) {
     const uint32_t peer = (uint32_t)(rank ^ 1);
     const uint32_t from = smem_u32(wave + (size_t)src * BLK + s0);
@@ -251,11 +250,32 @@ struct Tile {
                  "r"(from), "r"((uint32_t)n * (uint32_t)sizeof(float2)), "r"(bar)
                  : "memory");
   }
-  // row -> column: a round of the row-contiguous stage finishes T / R1 whole
-  // rows; column -> row: a round of the column-strided stage finishes T /
-  // ROWS consecutive n2, i.e. NB runs of T / ROWS rows of the block
-  static constexpr bool ROW_ROUNDS = XB && T % R1 == 0 && TC % T == 0;
-  static constexpr bool COL_ROUNDS = XB && T % ROWS == 0 && TS % T == 0;
+  __device__ static void publish_warp() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+  }
+  // Row -> column, after the row-contiguous round whose first task is that
+  // of lane 0 (a): the warp's tasks (r, k1) of the off-diagonal block
+  // b = rank ^ 1 cover whole 16-column groups, contiguous along each row.
+  __device__ static void push_row_round(float2* wave, int rank, int a) {
+    const int b = rank ^ 1;
+    const int lane = threadIdx.x & 31;
+    const int r = a / R1 + lane;  // one lane per row the warp touches
+    if (lane < 32 / R1 + 2 && r < ROWS) {
+      const int lo = max(a - R1 * r, NB * b), hi = min(a + 32 - R1 * r, NB * b + NB);
+      if (lo < hi) push(wave, rank, 1, 2, 1, r * ROWS + R2 * (lo - NB * b), R2 * (hi - lo));
+    }
+  }
+  // Column -> row, after the column-strided round whose first task is that
+  // of lane 0 (a): one n2 and 32 consecutive columns, i.e. 32 contiguous
+  // slots in each of the NB off-diagonal rows n2 + R2 j.
+  __device__ static void push_col_round(float2* wave, int rank, int a) {
+    const int lane = threadIdx.x & 31;
+    if (lane < NB) {
+      const int n2 = a / ROWS, cc0 = a % ROWS;
+      push(wave, rank, 2, 1, 0, (n2 + R2 * lane) * ROWS + cc0, 32);
+    }
+  }
 
   __device__ static void init_tables(float2* twS, float2* twC, int* fsq) {
     if constexpr (XB) {
@@ -406,17 +426,12 @@ struct Tile {
         // the off-diagonal one goes to the partner's column-layout buffer
 #pragma unroll
         for (int m = 0; m < R2; m += 2) st_pair(wave, rslot(rank, b, r, cc0 + m), x[m], x[m + 1]);
-        if constexpr (DIR < 0 && ROW_ROUNDS) {
-          constexpr int RR = T / R1;  // rows finished per round
-          publish();
-          if (threadIdx.x == 0) push(wave, rank, 1, 2, 1, t * RR * ROWS, RR * ROWS);
+        if constexpr (DIR < 0 && XB) {
+          publish_warp();
+          push_row_round(wave, rank, (int)(threadIdx.x & ~31u) + t * T);
         }
       }
       if constexpr (DIR < 0 && G > 1) {
-        if constexpr (!ROW_ROUNDS) {
-          publish();
-          if (threadIdx.x == 0) push(wave, rank, 1, 2, 1, 0, BLK);
-        }
         exchange_wait(wave, 1);
       } else {
         __syncthreads();
@@ -482,18 +497,13 @@ struct Tile {
           // the off-diagonal one goes to the partner's row-layout buffer)
 #pragma unroll
           for (int i = 0; i < R1; ++i) wave[cslot(rank, i / NB, n2 + R2 * (i % NB), cc)] = x[i];
-          if constexpr (G > 1 && COL_ROUNDS) {
-            constexpr int RN = T / ROWS;  // consecutive n2 finished per round
-            publish();
-            if ((int)threadIdx.x < NB) push(wave, rank, 2, 1, 0, (RN * t + R2 * (int)threadIdx.x) * ROWS, RN * ROWS);
+          if constexpr (XB) {
+            publish_warp();
+            push_col_round(wave, rank, (int)(threadIdx.x & ~31u) + t * T);
           }
         }
       }
       if constexpr (DIR > 0 && G > 1) {
-        if constexpr (!COL_ROUNDS) {
-          publish();
-          if (threadIdx.x == 0) push(wave, rank, 2, 1, 0, 0, BLK);
-        }
         exchange_wait(wave, 0);
       } else {
         __syncthreads();
