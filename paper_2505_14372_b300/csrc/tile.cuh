@@ -516,14 +516,23 @@ struct Tile {
   // i holds spectral slot pu = R2 k1 + i; op(pu, pv, v) is the pointwise
   // product; INV applies inverse s2' + twiddle and writes back in place; WB
   // (without INV) writes the spectral values back.  The caller synchronises.
+  // With one warp per k1 (T = 32 R1) a thread keeps its k1 in every task
+  // (columns lane + 32 t) and loads the inverse twiddles once per stage.
+  static constexpr bool WARP_K1 = T == 32 * R1 && ROWS % 32 == 0;
   template <bool FROM_SMEM, bool FWD, bool INV, bool WB = false, class Load, class Op>
   __device__ static void col_contig(float2* wave, const float2* twC, int rank, const Load& load,
                                     const Op& op) {
+    float2 tw[R2];
+    if constexpr (INV && WARP_K1) {
+#pragma unroll
+      for (int i = 1; i < R2; ++i) tw[i] = twC[i * R1 + (int)(threadIdx.x / 32)];
+    }
 #pragma unroll 1
     for (int t = 0; t < CPT; ++t) {
       const int id = threadIdx.x + t * T;
       if (TC % T != 0 && id >= TC) break;
-      const int k1 = id / ROWS, cc = id % ROWS;
+      const int k1 = WARP_K1 ? (int)(threadIdx.x / 32) : id / ROWS;
+      const int cc = WARP_K1 ? (int)(threadIdx.x % 32) + 32 * t : id % ROWS;
       const int b = k1 / NB, r0 = R2 * (k1 % NB);
       const int pv = rank * ROWS + cc;
       const int pu0 = R2 * k1;
@@ -541,7 +550,10 @@ struct Tile {
       if constexpr (INV) {
         Dft<R2, +1>::run(x);
 #pragma unroll
-        for (int i = 1; i < R2; ++i) x[i] = cmulc(x[i], twC[i * R1 + k1]);
+        for (int i = 1; i < R2; ++i) {
+          if constexpr (WARP_K1) x[i] = cmulc(x[i], tw[i]);
+          else x[i] = cmulc(x[i], twC[i * R1 + k1]);
+        }
 #pragma unroll
         for (int i = 0; i < R2; ++i) wave[cslot(rank, b, r0 + i, cc)] = x[i];
       } else if constexpr (WB) {
