@@ -215,12 +215,16 @@ struct Tile {
   __device__ static uint32_t bar_addr(const float2* wave, int which) {
     return smem_u32(wave) + (uint32_t)BAR_OFF + 8u * (uint32_t)which;
   }
-  // Waits until the partner's block for this layout switch has arrived
-  // (bounded: gives up after kExchangeSpin polls and flags it), then makes
-  // this CTA's own writes of the stage visible to all its threads.
+  // Waits until every warp of this CTA has finished the stage and the
+  // partner's block for this layout switch has arrived (bounded: gives up
+  // after kExchangeSpin polls and flags it).  The mbarrier is the stage's
+  // CTA barrier as well: each warp's arrival (after a warp barrier) releases
+  // its lanes' writes and the completed phase acquires them, so no
+  // __syncthreads is needed.
   __device__ static void exchange_wait(const float2* wave, int which, unsigned spin_limit = kExchangeSpin) {
     const uint32_t bar = bar_addr(wave, which);
     uint64_t tok = 0;
+    __syncwarp();
     if ((threadIdx.x & 31) == 0) tok = threadIdx.x == 0 ? mbar_arrive_tx(bar, BLK * 8) : mbar_arrive(bar);
     tok = __shfl_sync(0xffffffffu, tok, 0);
     unsigned it = 0;
@@ -230,7 +234,6 @@ struct Tile {
         break;
       }
     }
-    __syncthreads();
   }
 
   // Layout switch of the 2-CTA tile: the stage writes its results in place
