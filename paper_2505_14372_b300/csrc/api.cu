@@ -219,6 +219,29 @@ LaunchArgs one_problem(ptycho_ctx* c, const Layout& L, const ProblemDesc& d) {
   return a;
 }
 
+// The position-major kernel counts positions, not items, and takes its slot
+// as K entry-wave sets of S + 1 waves (the last for LSQML's probe direction).
+LaunchArgs one_position_problem(ptycho_ctx* c, const Layout& L, const ProblemDesc& d) {
+  LaunchArgs a = one_problem(c, L, d);
+  a.total = d.B;
+  a.slot_stride = (long long)c->g.K * (c->g.S + 1) * c->NP * (c->g.wave_prec ? 4 : 8);
+  return a;
+}
+ptycho::PosArgs pos_args(ptycho_ctx* c, const Layout& L) {
+  ptycho::PosArgs F{};
+  F.Abuf = reinterpret_cast<float2*>(c->arena + L.pA);
+  F.Ibuf = reinterpret_cast<float*>(c->arena + L.pI);
+  F.astride = (long long)c->g.K * c->NP;
+  return F;
+}
+void set_pos_loss(ProblemDesc& d, const float* Iexp, double* lpart, int model, const ptycho_geom& g) {
+  d.Iexp = Iexp;
+  d.lpart = lpart;
+  d.model = model;
+  d.eps = (float)g.eps;
+  d.c = (float)g.c;
+}
+
 int check_call(ptycho_ctx* c, int B) {
   if (!c) return perr(PTYCHO_EINVAL, "context is NULL");
   if (B < 0 || B > c->max_batch)
@@ -276,17 +299,10 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   const int variant = epie ? ptycho::kVarEpie : c->g.wave_prec;
   if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
   if (!c->store && !vjp && c->pos_clusters > 0) {
-    ptycho::PosArgs F{};
-    F.Iexp = Iexp;
-    F.Abuf = reinterpret_cast<float2*>(c->arena + L.pA);
-    F.Ibuf = reinterpret_cast<float*>(c->arena + L.pI);
-    F.lpart = partials;
-    F.model = model;
-    F.eps = (float)c->g.eps;
-    F.c = (float)c->g.c;
+    const ptycho::PosArgs F = pos_args(c, L);
+    set_pos_loss(d, Iexp, partials, model, c->g);
     CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
-    LaunchArgs la = one_problem(c, L, d);
-    la.slot_stride = (long long)K * (c->g.S + 1) * c->NP * (c->g.wave_prec ? 4 : 8);
+    LaunchArgs la = one_position_problem(c, L, d);
     {
       Timed t(c, "adjoint", s);
       CK(c->ops->adjoint_pos(la, F, std::min(B, c->pos_clusters), variant, s));
@@ -691,17 +707,9 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
   float2* Phat = reinterpret_cast<float2*>(c->arena + L.Phat);
   float2* gPhat = reinterpret_cast<float2*>(c->arena + L.gPhat);
   double* partials = reinterpret_cast<double*>(c->arena + L.partials);
-  ptycho::PosArgs F{};
-  F.Iexp = I_exp_all;
-  F.Abuf = reinterpret_cast<float2*>(c->arena + L.pA);
-  F.Ibuf = reinterpret_cast<float*>(c->arena + L.pI);
-  F.lpart = partials;
-  F.model = ptycho::kModelEpie;  // the modulus-update seed
-  F.eps = (float)c->g.eps;
-  F.c = (float)c->g.c;
+  ptycho::PosArgs F = pos_args(c, L);
   F.gamma = opt->gamma;
   const int clusters = std::min((int)B, c->pos_clusters);
-  const long long stride = (long long)K * (S + 1) * NP * 8;
 
   // pass 1: update directions (into gO, gP) and the group's illumination
   {
@@ -716,8 +724,8 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
   ProblemDesc d = base_desc(c, L, O, pos_all, idx, B, n_pos);
   d.gO = c->gO;
   d.lsq_il = il;
-  LaunchArgs la = one_problem(c, L, d);
-  la.slot_stride = stride;
+  set_pos_loss(d, I_exp_all, partials, ptycho::kModelEpie, c->g);  // the modulus-update seed
+  LaunchArgs la = one_position_problem(c, L, d);
   {
     Timed t(c, "adjoint", s);
     CK(c->ops->adjoint_pos(la, F, clusters, ptycho::kVarLsqDir, s));
@@ -747,9 +755,8 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
   CK(cudaMemsetAsync(denP, 0, (size_t)B * 8, s));
   CK(cudaMemsetAsync(aw, 0, (size_t)nO * 4, s));
   CK(cudaMemsetAsync(AT, 0, (size_t)NP * 4, s));
-  ptycho::PosArgs F2 = F;
-  F2.lpart = partials + B;  // the loss of this pass is not used
   ProblemDesc d2 = base_desc(c, L, O, pos_all, idx, B, n_pos);
+  set_pos_loss(d2, I_exp_all, partials + B, ptycho::kModelEpie, c->g);  // the loss of this pass is not used
   d2.gO = c->gO;
   d2.lsq_dO = dO;
   d2.lsq_dPhat = dPhat;
@@ -758,12 +765,11 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
   d2.lsq_numP = numP;
   d2.lsq_denP = denP;
   d2.lsq_aw = aw;
-  LaunchArgs la2 = one_problem(c, L, d2);
-  la2.slot_stride = stride;
-  CK(cudaMemsetAsync(F2.lpart, 0, (size_t)B * 8, s));
+  LaunchArgs la2 = one_position_problem(c, L, d2);
+  CK(cudaMemsetAsync(d2.lpart, 0, (size_t)B * 8, s));
   {
     Timed t(c, "adjoint", s);
-    CK(c->ops->adjoint_pos(la2, F2, clusters, ptycho::kVarLsqStep, s));
+    CK(c->ops->adjoint_pos(la2, F, clusters, ptycho::kVarLsqStep, s));
   }
   {
     Timed t(c, "lsq_update", s);
@@ -867,12 +873,111 @@ int resident_slots(int N) {
   return ops ? ops->resident_clusters(true, false, kVarF32) : 0;
 }
 
-// One gradient step for several problems of the same window size: their
-// (position, mode) items share one forward launch and one adjoint launch.
-int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long slot_stride, unsigned* status,
-               cudaStream_t s) {
+size_t pos_scratch_bytes(int N, int kmodes, int smax) {
+  const size_t NP = (size_t)N * N, cl = (size_t)resident_slots(N);
+  return cl * ((size_t)kmodes * (smax + 1) * NP * 8 + (size_t)kmodes * NP * 8 + NP * 4);
+}
+PosScratch pos_scratch_at(char* base, int N, int kmodes, int smax) {
+  PosScratch p;
+  const size_t NP = (size_t)N * N;
+  p.clusters = resident_slots(N);
+  p.kmodes = kmodes;
+  p.smax = smax;
+  p.slot_bytes = (long long)kmodes * (smax + 1) * NP * 8;
+  p.slots = base;
+  p.A = reinterpret_cast<float2*>(base + (size_t)p.clusters * p.slot_bytes);
+  p.I = reinterpret_cast<float*>(reinterpret_cast<char*>(p.A) + (size_t)p.clusters * kmodes * NP * 8);
+  return p;
+}
+
+namespace {
+
+// Adam, norms and regularisers of one job after its gradient launch(es);
+// nl: loss partials at the start of its partials.
+int finish_job(const StepJob& J, const Layout& L, int nl, cudaStream_t s) {
+  ptycho_ctx* c = J.c;
+  double* partials = reinterpret_cast<double*>(c->arena + L.partials);
+  const long long nO = (long long)c->g.S * c->g.H * c->g.W, nP = (long long)c->g.K * c->NP;
+  CK(c->ops->probe_grad(reinterpret_cast<float2*>(c->arena + L.gPhat), c->gP, c->g.K, 0, s));
+  const bool reg = J.opt.reg_obj_l2 != 0.f || J.opt.reg_obj_tikhonov != 0.f || J.opt.reg_obj_layers != 0.f ||
+                   J.opt.reg_probe_l2 != 0.f || J.opt.reg_obj_tv != 0.f || J.opt.reg_obj_layers_tv != 0.f;
+  const int nr = reg ? kNormBlocks : 0;
+  if (reg)
+    CK(launch_regularize(J.O, c->gO, c->g.S, c->g.H, c->g.W, J.P, c->gP, nP, J.opt.reg_obj_l2, J.opt.reg_obj_tikhonov,
+                         J.opt.reg_obj_layers, J.opt.reg_probe_l2, J.opt.reg_obj_tv, J.opt.reg_obj_layers_tv,
+                         J.opt.reg_tv_eps, partials + nl, nr, s));
+  CK(launch_sumsq(c->gO, nO, partials + nl + nr, kNormBlocks, s));
+  CK(launch_sumsq(c->gP, nP, partials + nl + nr + kNormBlocks, kNormBlocks, s));
+  CK(launch_finalize(partials, nl + nr, 2 * kNormBlocks, J.stats, 1, s));
+  const double t = (double)J.t;
+  const float bc1 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta1, t)));
+  const float bc2 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta2, t)));
+  CK(launch_adam(J.O, J.mO, J.vO, c->gO, nO, J.opt.lr_O, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s));
+  if (J.opt.update_probe)
+    CK(launch_adam(J.P, J.mP, J.vP, c->gP, nP, J.opt.lr_P, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s));
+  return PTYCHO_OK;
+}
+
+// All jobs in one position-major loss + adjoint launch.
+int step_batch_pos(const StepJob* jobs, int n, const PosScratch& ps, unsigned* status, cudaStream_t s) {
+  const EngineOps* ops = jobs[0].c->ops;
+  LaunchArgs la{};
+  la.nd = n;
+  la.status = status;
+  la.slots = ps.slots;
+  la.slot_stride = ps.slot_bytes;
+  std::vector<Layout> L(n);
+  int total = 0;
+  for (int i = 0; i < n; ++i) {
+    const StepJob& J = jobs[i];
+    ptycho_ctx* c = J.c;
+    L[i] = make_layout(c->g, c->max_batch, false, 0);
+    CK(ops->probe_spectrum(J.P, reinterpret_cast<float2*>(c->arena + L[i].Phat), c->g.K, s));
+    CK(cudaMemsetAsync(c->arena + L[i].gPhat, 0, (size_t)c->g.K * c->NP * 8, s));
+    CK(cudaMemsetAsync(c->gO, 0, (size_t)c->g.S * c->g.H * c->g.W * 8, s));
+    double* partials = reinterpret_cast<double*>(c->arena + L[i].partials);
+    CK(cudaMemsetAsync(partials, 0, (size_t)J.B * 8, s));
+    ProblemDesc d = base_desc(c, L[i], reinterpret_cast<const ptycho_c64*>(J.O), J.pos, J.idx, J.B, J.n_pos);
+    d.gO = c->gO;
+    d.item0 = total;
+    set_pos_loss(d, J.Iexp, partials, c->g.loss, c->g);
+    total += J.B;
+    la.d[i] = d;
+  }
+  la.total = total;
+  PosArgs F{};
+  F.Abuf = ps.A;
+  F.Ibuf = ps.I;
+  F.astride = (long long)ps.kmodes * jobs[0].c->NP;
+  CK(ops->adjoint_pos(la, F, std::min(total, ps.clusters), kVarF32, s));
+  for (int i = 0; i < n; ++i) {
+    const int rc = finish_job(jobs[i], L[i], jobs[i].B, s);
+    if (rc) return rc;
+  }
+  return PTYCHO_OK;
+}
+
+}  // namespace
+
+// One gradient step for several problems of the same window size.
+int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long slot_stride, const PosScratch* ps,
+               unsigned* status, cudaStream_t s, int* tile_launches) {
+  if (tile_launches) *tile_launches = 0;
   if (n < 1 || n > kMaxDesc) return perr(PTYCHO_EINVAL, "step_batch: 1..16 jobs");
   const EngineOps* ops = jobs[0].c->ops;
+  bool pos = ps && ps->slots && ps->clusters > 0 && ops->has_variants;
+  for (int i = 0; i < n; ++i) {
+    const StepJob& J = jobs[i];
+    ptycho_ctx* c = J.c;
+    if (c->ops != ops || c->store) return perr(PTYCHO_EINVAL, "step_batch: mixed window sizes or stored waves");
+    if (J.B < 1 || J.B > c->max_batch) return perr(PTYCHO_EINVAL, "step_batch: bad group size");
+    if (c->g.K > (ps ? ps->kmodes : 0) || c->g.S > (ps ? ps->smax : 0) || c->g.wave_prec != PTYCHO_PREC_F32) pos = false;
+  }
+  if (pos) {
+    if (tile_launches) *tile_launches = 1;
+    return step_batch_pos(jobs, n, *ps, status, s);
+  }
+  if (tile_launches) *tile_launches = 2;
   LaunchArgs la{};
   la.nd = n;
   la.status = status;
@@ -884,8 +989,6 @@ int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long 
   for (int i = 0; i < n; ++i) {
     const StepJob& J = jobs[i];
     ptycho_ctx* c = J.c;
-    if (c->ops != ops || c->store) return perr(PTYCHO_EINVAL, "step_batch: mixed window sizes or stored waves");
-    if (J.B < 1 || J.B > c->max_batch) return perr(PTYCHO_EINVAL, "step_batch: bad group size");
     if ((long long)c->g.S * c->NP * (c->g.wave_prec ? 4 : 8) > slot_stride * 8)
       return perr(PTYCHO_EINVAL, "step_batch: slot too small");
     L[i] = make_layout(c->g, c->max_batch, false, 0);
@@ -910,27 +1013,8 @@ int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long 
   }
   CK(ops->adjoint(la, std::min(total, nslots), false, kVarF32, s));
   for (int i = 0; i < n; ++i) {
-    const StepJob& J = jobs[i];
-    ptycho_ctx* c = J.c;
-    double* partials = reinterpret_cast<double*>(c->arena + L[i].partials);
-    const long long nO = (long long)c->g.S * c->g.H * c->g.W, nP = (long long)c->g.K * c->NP;
-    CK(ops->probe_grad(reinterpret_cast<float2*>(c->arena + L[i].gPhat), c->gP, c->g.K, 0, s));
-    const bool reg = J.opt.reg_obj_l2 != 0.f || J.opt.reg_obj_tikhonov != 0.f || J.opt.reg_obj_layers != 0.f ||
-                     J.opt.reg_probe_l2 != 0.f || J.opt.reg_obj_tv != 0.f || J.opt.reg_obj_layers_tv != 0.f;
-    const int nr = reg ? kNormBlocks : 0;
-    if (reg)
-      CK(launch_regularize(J.O, c->gO, c->g.S, c->g.H, c->g.W, J.P, c->gP, nP, J.opt.reg_obj_l2,
-                           J.opt.reg_obj_tikhonov, J.opt.reg_obj_layers, J.opt.reg_probe_l2, J.opt.reg_obj_tv,
-                           J.opt.reg_obj_layers_tv, J.opt.reg_tv_eps, partials + nl[i], nr, s));
-    CK(launch_sumsq(c->gO, nO, partials + nl[i] + nr, kNormBlocks, s));
-    CK(launch_sumsq(c->gP, nP, partials + nl[i] + nr + kNormBlocks, kNormBlocks, s));
-    CK(launch_finalize(partials, nl[i] + nr, 2 * kNormBlocks, J.stats, 1, s));
-    const double t = (double)J.t;
-    const float bc1 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta1, t)));
-    const float bc2 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta2, t)));
-    CK(launch_adam(J.O, J.mO, J.vO, c->gO, nO, J.opt.lr_O, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s));
-    if (J.opt.update_probe)
-      CK(launch_adam(J.P, J.mP, J.vP, c->gP, nP, J.opt.lr_P, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s));
+    const int rc = finish_job(jobs[i], L[i], nl[i], s);
+    if (rc) return rc;
   }
   return PTYCHO_OK;
 }

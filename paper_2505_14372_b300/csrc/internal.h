@@ -28,10 +28,31 @@ struct StepJob {
   double* stats;        // device double[2]: loss, gradient norm
 };
 
+// Scratch of the position-major loss + adjoint kernel shared by the
+// problems of one window size: per cluster, the entry waves of up to kmodes
+// modes and smax + 1 waves each, the far fields of up to kmodes modes and
+// the mode-summed intensity.
+struct PosScratch {
+  char* slots = nullptr;     // [clusters][slot_bytes]
+  long long slot_bytes = 0;
+  float2* A = nullptr;       // [clusters][kmodes NP]
+  float* I = nullptr;        // [clusters][NP]
+  int clusters = 0, kmodes = 0, smax = 0;
+};
+// Bytes of a PosScratch for window N (clusters = resident_slots(N)).
+size_t pos_scratch_bytes(int N, int kmodes, int smax);
+// Carves a PosScratch out of one device allocation of pos_scratch_bytes.
+PosScratch pos_scratch_at(char* base, int N, int kmodes, int smax);
+
 int ctx_create_shared_slots(const ptycho_geom* geom, int max_batch, ptycho_ctx** out);
 size_t ctx_device_bytes(const ptycho_ctx* c);
 int resident_slots(int N);
-int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long slot_stride, unsigned* status,
-               cudaStream_t s);
+// One gradient step for each job (all of one window size).  With `ps` (and
+// every job's modes and slices within it) one position-major launch covers
+// all jobs; otherwise one forward and one recomputing adjoint launch over
+// their (position, mode) items, with `slots` as the adjoint's scratch.
+// *tile_launches: the tile-kernel launches the step made (1 or 2).
+int step_batch(const StepJob* jobs, int n, float2* slots, int nslots, long long slot_stride, const PosScratch* ps,
+               unsigned* status, cudaStream_t s, int* tile_launches);
 
 }  // namespace ptycho

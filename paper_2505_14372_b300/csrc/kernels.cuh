@@ -450,7 +450,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_consta
 
 // Loss + adjoint with the entry waves recomputed, one cluster per scan
 // position (position-major, one launch per step, no waits between
-// clusters).  For position j the cluster runs the forward pass of every mode
+// clusters; the positions of several problems of one window size may share
+// a launch).  For position j the cluster runs the forward pass of every mode
 // k (entry waves to part k of its slot, far field A_k to its scratch, the
 // intensity summed over modes in its scratch), applies the noise model to
 // the mode sum (loss into lpart[j], seed weight 2 l'(I) / NP in place of I),
@@ -467,17 +468,19 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
   TL::init_tables(sm.twS, sm.twC, sm.fsq);
   constexpr int N = TL::N;
   constexpr float inv = 1.0f / (float)TL::NP;
-  const ProblemDesc& D = L.d[0];
-  const int K = D.K;
   const int cid = cluster_id<TL>();
   char* slot = L.slots + (size_t)cid * L.slot_stride;
-  // one mode's entry waves (and, in the LSQML step pass, its shifted probe direction)
-  const size_t wstride = (size_t)(D.S + Var<V>::extra_waves) * TL::NP * Var<V>::wave_bytes;
-  float2* Ab = F.Abuf + (size_t)cid * K * TL::NP;
+  float2* Ab = F.Abuf + (size_t)cid * F.astride;
   float* Ib = F.Ibuf + (size_t)cid * TL::NP;
 #pragma unroll 1
-  for (int j = cid; j < D.B; j += n_clusters<TL>()) {
-    ItemGeo g = item_geo<TL>(D, j * K);
+  for (int jg = cid; jg < L.total; jg += n_clusters<TL>()) {
+    // position j of problem D (item0: its first position in the launch)
+    const ProblemDesc& D = find_desc(L, jg);
+    const int j = jg - D.item0;
+    const int K = D.K;
+    // one mode's entry waves (and, in the LSQML step pass, its shifted probe direction)
+    const size_t wstride = (size_t)(D.S + Var<V>::extra_waves) * TL::NP * Var<V>::wave_bytes;
+    ItemGeo g = item_geo<TL>(D, D.item0 + j * K);
     TL::sync_cluster();
     if (!g.ok) {  // every mode of this position skips it
       if (threadIdx.x == 0 && rank == 0) atomicOr(L.status, PTYCHO_STATUS_OUT_OF_BOUNDS);
@@ -485,7 +488,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
     }
     make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
     __syncthreads();
-    const float* E = F.Iexp + (size_t)g.jj * TL::NP;
+    const float* E = D.Iexp + (size_t)g.jj * TL::NP;
     float lsum = 0.f;
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
           Ib[p] = I;
         } else {
           float l, dl;
-          noise_model(F.model, F.eps, F.c, I, __ldg(E + TL::nat(pu) * N + TL::nat(pv)), l, dl);
+          noise_model(D.model, D.eps, D.c, I, __ldg(E + TL::nat(pu) * N + TL::nat(pv)), l, dl);
           lsum += l;
           Ib[p] = 2.0f * dl * inv;
         }
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
       double sd = lsum;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
-      if ((threadIdx.x & 31) == 0) atomicAdd(F.lpart + j, sd);
+      if ((threadIdx.x & 31) == 0) atomicAdd(D.lpart + j, sd);
     }
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {

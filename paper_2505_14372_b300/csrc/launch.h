@@ -35,7 +35,13 @@ struct ProblemDesc {
   int S, K, H, W, B;
   int npos;             // rows of pos (and of the pattern array) idx may select
   int blT;              // band limit keeps f_u^2 + f_v^2 <= blT; < 0: off
-  int item0;            // first global item of this problem
+  int item0;            // first global item (position-major kernel: position) of this problem
+  // position-major loss + adjoint: measured patterns [npos][NP] (natural
+  // order), loss per position [B] (zeroed per launch) and the noise model
+  const float* Iexp;
+  double* lpart;
+  int model;
+  float eps, c;
   // ePIE (null for the gradient): max |O_s|^2 per slice [S] and max |psi_s|^2
   // per item and slice [B][K][S], both as float bits (atomicMax)
   const unsigned* omax;
@@ -67,13 +73,12 @@ struct LaunchArgs {
 // per scan position runs the forward pass of every mode, the noise model on
 // the mode sum, then the backward pass of every mode.  Per-cluster scratch:
 // far fields and intensity / seed weights (and K entry-wave sets in the slot).
+// The positions of a launch are those of all its problems in order
+// (LaunchArgs::total of them, ProblemDesc::item0 the first of each).
 struct PosArgs {
-  const float* Iexp;   // [npos][NP] measured patterns, natural order
-  float2* Abuf;        // [clusters][K][NP] far fields F(phi), slot order
+  float2* Abuf;        // [clusters][astride] far fields F(phi) of the modes, slot order
   float* Ibuf;         // [clusters][NP] mode-summed intensity, then 2 l'(I) / NP
-  double* lpart;       // [B] loss per position (zeroed per launch)
-  int model;           // noise model
-  float eps, c;
+  long long astride;   // float2 per cluster in Abuf (>= K NP of every problem)
   float gamma;         // LSQML step-size regulariser
 };
 

@@ -6,10 +6,12 @@
 // budget as memory and slots free up; each admitted request keeps its object,
 // probe, Adam moments, positions and patterns resident.  Every scheduling
 // tick issues one gradient step (one group) for each active request: the
-// requests that share a window size ride in one forward launch and one
-// adjoint launch (their items from several problem descriptors), and the
-// window-size classes run on their own streams, so their work overlaps on the
-// device.  Per-iteration latency is measured with CUDA events.
+// requests that share a window size ride in one position-major loss +
+// adjoint launch (their positions from several problem descriptors; when
+// the budget has no room for its scratch, in one forward and one
+// recomputing adjoint launch instead), and the window-size classes run on
+// their own streams, so their work overlaps on the device.  Per-iteration
+// latency is measured with CUDA events.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +37,7 @@ using ptycho::StepJob;
 namespace {
 
 constexpr int kMaxSlices = 32;       // slot scratch is sized for this many slices
+constexpr int kPosModes = 8;         // position-major scratch holds this many modes
 constexpr int kMaxInflight = 2;      // ticks queued per stream
 constexpr int kClasses = 4;          // window sizes 64, 128, 192, 256
 const int kN[kClasses] = {64, 128, 192, 256};
@@ -87,6 +90,11 @@ struct Class {
   int nslots = 0;
   long long stride = 0;
   size_t bytes = 0;
+  // scratch of the position-major step (null when the budget has no room
+  // for it: the class then runs the forward + recomputing adjoint launches)
+  char* pos_mem = nullptr;
+  size_t pos_bytes = 0;
+  ptycho::PosScratch ps;
   std::deque<Tick> inflight;
   cudaEvent_t last_ev = nullptr;  // end of the previous tick on this stream
   size_t rr = 0;                  // round-robin cursor
@@ -187,6 +195,15 @@ int ptycho_server::admit(Request* r) {
       return PTYCHO_ENOMEM;
     }
     slot_bytes += C.bytes;
+    const size_t pb = ptycho::pos_scratch_bytes(g.h, kPosModes, kMaxSlices);
+    if (admitted_bytes + slot_bytes + pb <= budget && cudaMalloc(&C.pos_mem, pb) == cudaSuccess) {
+      C.pos_bytes = pb;
+      C.ps = ptycho::pos_scratch_at(C.pos_mem, g.h, kPosModes, kMaxSlices);
+      slot_bytes += pb;
+    } else {
+      cudaGetLastError();
+      C.pos_mem = nullptr;
+    }
   }
   ptycho_geom gg = g;
   gg.dz = r->dz.empty() ? nullptr : r->dz.data();
@@ -357,10 +374,12 @@ bool ptycho_server::issue_ticks() {
       tk.who.push_back({r, closes});
     }
     if (jobs.empty()) continue;
-    int rc = ptycho::step_batch(jobs.data(), (int)jobs.size(), C.slots, C.nslots, C.stride, status, C.stream);
+    int tl = 0;
+    int rc = ptycho::step_batch(jobs.data(), (int)jobs.size(), C.slots, C.nslots, C.stride,
+                                C.pos_mem ? &C.ps : nullptr, status, C.stream, &tl);
     if (rc == PTYCHO_OK && cudaEventCreate(&tk.ev) == cudaSuccess && cudaEventRecord(tk.ev, C.stream) == cudaSuccess) {
       C.inflight.push_back(tk);
-      n_launches += 2;
+      n_launches += tl;
       any = true;
     } else {
       cudaGetLastError();
@@ -456,6 +475,7 @@ int ptycho_server_destroy(ptycho_server* s) {
     for (Tick& t : C.inflight) cudaEventDestroy(t.ev);
     C.inflight.clear();
     cudaFree(C.slots);
+    cudaFree(C.pos_mem);
     if (C.stream) cudaStreamDestroy(C.stream);
   }
   for (auto& kv : s->all) s->release_device(kv.second.get());
