@@ -1,5 +1,6 @@
 // Tensor-core variant of the FFT tile: the same layouts, stages, fusions
-// and cluster exchange as Tile, with every R1- and R2-point DFT evaluated by
+// and cluster exchange (in-place results, the off-diagonal block as one bulk
+// copy per switch) as Tile, with every R1- and R2-point DFT evaluated by
 // tc_dft8 (8 tasks per warp per call) instead of the register butterflies.
 // Exposes the interface the kernels use, so the forward/adjoint kernels are
 // instantiated unchanged on it.
@@ -96,10 +97,6 @@ struct TileTC : Base {
     const int warp = threadIdx.x >> 5;
     TcMat<MODE> M;
     load_mat<R2, DIR>(M);
-    const uint32_t w0 = smem_u32(wave);
-    uint32_t base[G];
-#pragma unroll
-    for (int b = 0; b < G; ++b) base[b] = G > 1 ? cluster_map(w0, (uint32_t)b) : w0;
     auto sl = [&](int id, int e) {
       const int r = id / R1, k1 = id % R1;
       return rslot(rank, k1 / NB, r, R2 * (k1 % NB) + e);
@@ -109,22 +106,27 @@ struct TileTC : Base {
       tc_dft8<MODE, R2>(
           M, 8 * q, [&](int id, int e) { return wave[sl(id, e)]; },
           [&](int id, int m, float2 v) {
-            const int r = id / R1, k1 = id % R1, b = k1 / NB;
             if constexpr (DIR > 0) {
-              if (m) v = cmulc(v, twC[m * R1 + k1]);
-              wave[sl(id, m)] = v;
-            } else {
-              if (G == 1 || b == rank) wave[sl(id, m)] = v;
-              else st_cluster(base[b] + 8u * (uint32_t)cslot(b, rank, r, R2 * (k1 % NB) + m), v);
+              if (m) v = cmulc(v, twC[m * R1 + id % R1]);
             }
+            wave[sl(id, m)] = v;  // in place; the off-diagonal block is sent whole below
           });
     }
     if constexpr (DIR < 0 && G > 1) {
-      cluster_arrive_release();
-      cluster_wait();
+      send_block(wave, rank, 1, 2, 1);
+      Base::exchange_wait(wave, 1);
     } else {
       __syncthreads();
     }
+  }
+  // the layout switch of the 2-CTA tile: every thread's in-place results
+  // visible to the copy engine, then the off-diagonal block (slots of block
+  // src) goes to the partner's idle buffer dst as one bulk copy counted on
+  // its mbarrier `which`
+  __device__ static void send_block(float2* wave, int rank, int src, int dst, int which) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) Base::push(wave, rank, src, dst, which, 0, BLK);
   }
 
   // ---- column strided ---------------------------------------------------
@@ -133,10 +135,6 @@ struct TileTC : Base {
     const int warp = threadIdx.x >> 5;
     TcMat<MODE> M;
     load_mat<R1, DIR>(M);
-    const uint32_t w0 = smem_u32(wave);
-    uint32_t base[G];
-#pragma unroll
-    for (int b = 0; b < G; ++b) base[b] = G > 1 ? cluster_map(w0, (uint32_t)b) : w0;
     auto sl = [&](int id, int e) {
       const int n2 = id / ROWS, cc = id % ROWS;
       return cslot(rank, e / NB, n2 + R2 * (e % NB), cc);
@@ -146,19 +144,16 @@ struct TileTC : Base {
       tc_dft8<MODE, R1>(
           M, 8 * q, [&](int id, int e) { return wave[sl(id, e)]; },
           [&](int id, int m, float2 v) {
-            const int n2 = id / ROWS, cc = id % ROWS;
             if constexpr (DIR < 0) {
-              wave[sl(id, m)] = m ? cmul(v, twS[m * R2 + n2]) : v;
+              wave[sl(id, m)] = m ? cmul(v, twS[m * R2 + id / ROWS]) : v;
             } else {
-              const int b = m / NB, r = n2 + R2 * (m % NB);
-              if (G == 1 || b == rank) wave[rslot(rank, b, r, cc)] = v;
-              else st_cluster(base[b] + 8u * (uint32_t)rslot(b, rank, r, cc), v);
+              wave[sl(id, m)] = v;  // natural row n2 + R2 (m % NB) of block m / NB, in place
             }
           });
     }
     if constexpr (DIR > 0 && G > 1) {
-      cluster_arrive_release();
-      cluster_wait();
+      send_block(wave, rank, 2, 1, 0);
+      Base::exchange_wait(wave, 0);
     } else {
       __syncthreads();
     }
