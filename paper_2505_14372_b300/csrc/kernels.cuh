@@ -235,7 +235,7 @@ __device__ void forward_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
       // non-negative floats order like their bit patterns
       if ((threadIdx.x & 31) == 0) atomicMax(D.wmax + ((size_t)g.j * D.K + g.k) * D.S + s, __float_as_uint(lm));
     }
-    __syncthreads();
+    TL::row_sync();  // the row -> column stage stays within rows until its exchange
     TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
     if (s + 1 < D.S) {
       TL::template col_contig<true, true, true>(sm.wave, sm.twC, rank, NoLoad{},
@@ -312,7 +312,7 @@ __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
                                              v = cconjmul(p.o, v);
                                            });
     }
-    __syncthreads();
+    TL::row_sync();  // the row -> column stage stays within rows until its exchange
     TL::forward_mid(sm.wave, sm.twS, sm.twC, rank);
     if (s > 0) {
       TL::template col_contig<true, true, true>(sm.wave, sm.twC, rank, NoLoad{},

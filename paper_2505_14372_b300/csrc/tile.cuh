@@ -164,6 +164,25 @@ struct Tile {
   static_assert(!XB || (TC % T == 0 && TS % T == 0 && ROWS % 32 == 0 && NB * 2 == R1),
                 "2-CTA exchange: whole rounds, warps of 32 consecutive columns");
 
+  // Row stages of the 2-CTA tile: NG groups of GT threads, group g owning
+  // rows [RG g, RG (g + 1)) in both row stages, so the barriers between them
+  // (no data crosses rows) are per group, named barrier 1 + g.
+  static constexpr int NG = 4, GT = T / NG, RG = ROWS / NG;
+  static constexpr bool ROWG = XB && T % NG == 0 && GT % 32 == 0 && GT % R1 == 0 && GT % R2 == 0 &&
+                               ROWS % NG == 0 && (RG * R1) % GT == 0 && (RG * R2) % GT == 0;
+  // id of this thread's task in round t of a row stage, tasks enumerated
+  // row-major with PER tasks per row
+  template <int PER>
+  __device__ static __forceinline__ int row_task(int t) {
+    if constexpr (ROWG) return RG * PER * (int)(threadIdx.x / GT) + (int)(threadIdx.x % GT) + GT * t;
+    else return (int)threadIdx.x + T * t;
+  }
+  // barrier between two row stages
+  __device__ static void row_sync() {
+    if constexpr (ROWG) asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / GT)), "r"(GT) : "memory");
+    else __syncthreads();
+  }
+
   // natural DFT bin held by spectral slot p, and slot of natural bin n
   __host__ __device__ static constexpr int nat(int p) { return p / R2 + R1 * (p % R2); }
   __host__ __device__ static constexpr int perm(int n) { return n / R1 + R2 * (n % R1); }
@@ -321,7 +340,7 @@ struct Tile {
     }
 #pragma unroll 1
     for (int t = 0; t < SPT; ++t) {
-      const int id = threadIdx.x + t * T;
+      const int id = row_task<R2>(t);
       if (TS % T != 0 && id >= TS) break;
       const int r = id / R2, n2 = id % R2;
       const int grow = rank * ROWS + r;
@@ -410,7 +429,7 @@ struct Tile {
       }
 #pragma unroll 1
       for (int t = 0; t < CPT; ++t) {
-        const int id = threadIdx.x + t * T;
+        const int id = row_task<R1>(t);
         if (TC % T != 0 && id >= TC) break;
         const int r = id / R1, k1 = id % R1;
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
@@ -431,11 +450,13 @@ struct Tile {
         for (int m = 0; m < R2; m += 2) st_pair(wave, rslot(rank, b, r, cc0 + m), x[m], x[m + 1]);
         if constexpr (DIR < 0 && XB) {
           publish_warp();
-          push_row_round(wave, rank, (int)(threadIdx.x & ~31u) + t * T);
+          push_row_round(wave, rank, id - (int)(threadIdx.x & 31));  // the warp's first task
         }
       }
       if constexpr (DIR < 0 && G > 1) {
         exchange_wait(wave, 1);
+      } else if constexpr (DIR > 0) {
+        row_sync();  // the next stage (real-space row stage) stays within rows
       } else {
         __syncthreads();
       }

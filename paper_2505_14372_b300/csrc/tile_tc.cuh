@@ -37,6 +37,8 @@ struct TileTC : Base {
   using Base::sync_cluster;
 
   __device__ static const uint32_t* table(int m) { return g_tc_tables[MODE - 1][m]; }
+  // this tile's row stages spread rows over all warps
+  __device__ static void row_sync() { __syncthreads(); }
   template <int R, int DIR>
   __device__ static void load_mat(TcMat<MODE>& M) {
     M.load(table((R == R1 && R1 != R2 ? 0 : 2) + (DIR > 0 ? 1 : 0)));
