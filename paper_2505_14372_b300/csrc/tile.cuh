@@ -22,11 +22,13 @@
 // is a block transpose across the cluster: element (CTA c, block b, row r,
 // column cc) moves to (CTA b, block c, r, cc); it is fused into the last
 // stage of a row pass (row -> column) and of an inverse column pass (column
-// -> row).  For G = 2 that stage writes its results in place and the
-// off-diagonal block (the same swizzle in both CTAs) goes to the partner's
-// idle buffer as bulk shared::cluster copies, one per finished round of
-// tasks, so the transfer overlaps the remaining rounds; the copies count
+// -> row).  For G = 2 that stage writes its results in place and every
+// warp sends the off-diagonal slots it has just finished (the same swizzle
+// in both CTAs) to the partner's idle buffer as bulk shared::cluster
+// copies, so the transfer overlaps the rest of the stage; the copies count
 // their bytes on the partner's mbarrier (no cluster barrier per switch).
+// Between the two row stages no data crosses rows, so for G = 2 groups of
+// warps that own whole rows meet at their own named barriers there.
 // G = 4 stages the block in registers and writes it with
 // st.shared::cluster between two cluster barriers.
 //
