@@ -357,7 +357,9 @@ typedef struct {
   int64_t submitted, admitted, finished, failed;
   int64_t queue_depth;
   size_t admitted_bytes, budget_bytes;
-  int64_t launches;            /* shared forward/adjoint launches issued */
+  int64_t launches;            /* shared tile-kernel launches issued (per tick and window size: one
+                                  position-major launch, or a forward + adjoint pair when the
+                                  budget has no room for its scratch) */
   double positions_per_s;      /* over the server's busy time */
   double p50_iter_ms, p99_iter_ms; /* per-iteration latency over finished steps */
 } ptycho_server_stats;

@@ -30,9 +30,9 @@ REQS = [
 ]
 
 
-def run_alone(i, iters=3, batch=8):
+def run_alone(i, iters=3, batch=8, budget=8 * GB):
     r = request(**REQS[i])
-    srv = Server(8 * GB, 4)
+    srv = Server(budget, 4)
     t = srv.submit(r[0], r[2], r[3], r[1], iterations=iters, batch=batch, seed=11, opt=adam_opt(1e-2, 1e-3))
     srv.wait(t)
     out = srv.poll(t, r[0])
@@ -41,10 +41,15 @@ def run_alone(i, iters=3, batch=8):
     return out, st
 
 
-def test_served_result_equals_plain_step_path():
+@pytest.mark.parametrize("budget,launches_per_step", [(8 * GB, 1), (2 * GB, 2)])
+def test_served_result_equals_plain_step_path(budget, launches_per_step):
     geom, P, pos, I_exp = request(**REQS[0])
-    out, _ = run_alone(0)
+    out, st = run_alone(0, budget=budget)
     assert out["state"] == "done" and out["iterations_done"] == 3
+    # 8 GB holds the position-major scratch of the 64 x 64 class (one tile
+    # launch per step); 2 GB does not (a forward + recomputing adjoint pair);
+    # 3 iterations of 4 groups, one request per tick
+    assert st["launches"] == 12 * launches_per_step
     # plain path: same groups, same Adam steps, one ptycho_step per group
     ctx = Context(geom, max_batch=8)
     Od = torch.ones((geom.S, geom.H, geom.W), dtype=torch.complex64, device="cuda")
