@@ -123,6 +123,12 @@ struct ptycho_ctx {
   char* lsq = nullptr;    // LSQML buffers, allocated on first use
   size_t lsq_bytes = 0;
   int res_fwd = 1, res_adj = 1, res_rec = 1;
+  // host-buffer steps: the patterns after the first round of positions are
+  // copied on their own stream while that round computes (split_B1 > 0
+  // during such a step)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copied = nullptr;
+  int split_B1 = 0;
   // timing
   bool timing = false;
   struct Pending {
@@ -302,10 +308,27 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
     const ptycho::PosArgs F = pos_args(c, L);
     set_pos_loss(d, Iexp, partials, model, c->g);
     CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
-    LaunchArgs la = one_position_problem(c, L, d);
+    // split: positions [0, B1) first, then the rest once their patterns
+    // (copied on another stream) are in; idx-free groups only
+    const int B1 = (c->split_B1 > 0 && c->split_B1 < B && !idx) ? c->split_B1 : B;
     {
+      LaunchArgs la = one_position_problem(c, L, d);
+      la.d[0].B = B1;
+      la.total = B1;
       Timed t(c, "adjoint", s);
-      CK(c->ops->adjoint_pos(la, F, std::min(B, c->pos_clusters), variant, s));
+      CK(c->ops->adjoint_pos(la, F, std::min(B1, c->pos_clusters), variant, s));
+    }
+    if (B1 < B) {
+      ProblemDesc d2 = d;
+      d2.pos = pos + 2 * (size_t)B1;
+      d2.Iexp = Iexp + (size_t)B1 * c->NP;
+      d2.lpart = partials + B1;
+      d2.B = B - B1;
+      d2.npos = B - B1;
+      LaunchArgs la2 = one_position_problem(c, L, d2);
+      CK(cudaStreamWaitEvent(s, c->copied, 0));
+      Timed t(c, "adjoint", s);
+      CK(c->ops->adjoint_pos(la2, F, std::min(B - B1, c->pos_clusters), variant, s));
     }
     *nl_out = B;
     Timed t(c, "probe_grad", s);
@@ -434,6 +457,8 @@ int ptycho_create(const ptycho_geom* geom, int32_t max_batch, size_t scratch_bud
 
 int ptycho_destroy(ptycho_ctx* c) {
   if (!c) return PTYCHO_OK;
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->copied) cudaEventDestroy(c->copied);
   for (auto& p : c->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -610,13 +635,35 @@ int ptycho_step_host(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
   float* dpos = reinterpret_cast<float*>(c->arena + L.stage_pos);
   float* dI = reinterpret_cast<float*>(c->arena + L.stage_I);
   double* stats = reinterpret_cast<double*>(c->arena + L.stats);
+  // With the position-major step and more than one round of positions, only
+  // the first round's patterns are copied ahead of the compute; the rest
+  // travel on the context's copy stream while that round runs.
+  int B1 = B;
+  if (!c->store && c->pos_clusters > 0 && B > c->pos_clusters) {
+    if (!c->copy_stream) {
+      CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&c->copied, cudaEventDisableTiming));
+    }
+    B1 = c->pos_clusters;
+  }
   if (B > 0) {
     Timed t(c, "h2d", s);
     CK(cudaMemcpyAsync(dpos, pos_host, (size_t)B * 2 * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(dI, I_exp_host, (size_t)B * c->NP * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dI, I_exp_host, (size_t)B1 * c->NP * 4, cudaMemcpyHostToDevice, s));
+  }
+  if (B1 < B) {
+    // the staging rows are free: the previous call synchronised its stream
+    CK(cudaMemcpyAsync(dI + (size_t)B1 * c->NP, I_exp_host + (size_t)B1 * c->NP, (size_t)(B - B1) * c->NP * 4,
+                       cudaMemcpyHostToDevice, c->copy_stream));
+    CK(cudaEventRecord(c->copied, c->copy_stream));
+    c->split_B1 = B1;
   }
   rc = step_impl(c, O, P, st, opt, dpos, dI, B, nullptr, B, stats, s);
-  if (rc) return rc;
+  c->split_B1 = 0;
+  if (rc) {
+    if (B1 < B) cudaStreamSynchronize(c->copy_stream);
+    return rc;
+  }
   double h[2] = {0, 0};
   CK(cudaMemcpyAsync(h, stats, 16, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
