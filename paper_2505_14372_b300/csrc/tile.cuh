@@ -166,12 +166,12 @@ struct Tile {
   static_assert(!XB || (TC % T == 0 && TS % T == 0 && ROWS % 32 == 0 && NB * 2 == R1),
                 "2-CTA exchange: whole rounds, warps of 32 consecutive columns");
 
-  // Row stages of the 2-CTA tile: NG groups of GT threads, group g owning
-  // rows [RG g, RG (g + 1)) in both row stages, so the barriers between them
-  // (no data crosses rows) are per group, named barrier 1 + g.
+  // Row stages: NG groups of GT threads, group g owning rows
+  // [RG g, RG (g + 1)) in both row stages, so the barriers between them (no
+  // data crosses rows) are per group, named barrier 1 + g.
   static constexpr int NG = 4, GT = T / NG, RG = ROWS / NG;
-  static constexpr bool ROWG = XB && T % NG == 0 && GT % 32 == 0 && GT % R1 == 0 && GT % R2 == 0 &&
-                               ROWS % NG == 0 && (RG * R1) % GT == 0 && (RG * R2) % GT == 0;
+  static constexpr bool ROWG = T % NG == 0 && GT % 32 == 0 && GT % R1 == 0 && GT % R2 == 0 && ROWS % NG == 0 &&
+                               (RG * R1) % GT == 0 && (RG * R2) % GT == 0;
   // id of this thread's task in round t of a row stage, tasks enumerated
   // row-major with PER tasks per row
   template <int PER>
@@ -388,7 +388,7 @@ struct Tile {
       float2 x[CPT][R2];
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
-        const int id = threadIdx.x + t * T;
+        const int id = row_task<R1>(t);
         if (TC % T != 0 && id >= TC) continue;
         const int r = id / R1, k1 = id % R1;
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
@@ -404,7 +404,7 @@ struct Tile {
       const uint32_t w0 = smem_u32(wave);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
-        const int id = threadIdx.x + t * T;
+        const int id = row_task<R1>(t);
         if (TC % T != 0 && id >= TC) continue;
         const int r = id / R1, k1 = id % R1;
         const int b = k1 / NB, cc0 = R2 * (k1 % NB);
