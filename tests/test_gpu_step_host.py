@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from gpu_util import dev, host, problem, rel_l2
-from paper_2505_14372_b300 import AdamState, Context, adam_opt
+from paper_2505_14372_b300 import AdamState, Context, PtychoError, adam_opt
 
 pytestmark = pytest.mark.gpu
 
@@ -35,3 +35,16 @@ def test_step_host_equals_device_step(B):
     assert abs(loss2 - loss1) <= 1e-6 * abs(loss1)
     # gradients are scattered with float atomics: equal up to summation order
     assert rel_l2(host(O2), host(O1)) < 1e-6 and rel_l2(host(P2), host(P1)) < 1e-6
+
+
+def test_step_host_rejects_a_window_outside_the_object():
+    N, B = 64, 4
+    geom, og, P, O, pos = problem(53, 1, 1, N, 96, 96, B)
+    geom.waves = "recompute"
+    ctx = Context(geom, max_batch=B)
+    bad = pos.copy()
+    bad[2] = [96 - N + 1.0, 3.0]  # the window's last row leaves the object
+    I_exp = np.ones((B, N, N), np.float32)
+    with pytest.raises(PtychoError) as e:
+        ctx.step_host(dev(O), dev(P), AdamState(geom), adam_opt(1e-3, 1e-4), bad, I_exp)
+    assert e.value.code == -2
