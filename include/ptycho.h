@@ -291,6 +291,17 @@ int ptycho_make_groups(int32_t P, int32_t B, uint64_t seed, int64_t iteration, i
  * ptycho_set_timing(ctx, 1).  names/ms are host arrays of length cap;
  * returns the number of entries, or a negative code. */
 int ptycho_set_timing(ptycho_ctx* ctx, int32_t enable);
+
+/* Adam step count kept in device memory, so that a step captured in a CUDA
+ * graph replays with the right bias corrections (§3.2 solver).  With t_dev
+ * set (one int64 in device memory, owned by the caller), every ptycho_step /
+ * ptycho_step_host of this context takes t = *t_dev + 1, stores it back and
+ * computes the corrections 1 / (1 - beta^t) on the stream, before its Adam
+ * update; the host count of ptycho_adam is then not used for them (it is
+ * still incremented).  t_dev = NULL returns to the host count.  Not a
+ * stream call: allocates 8 bytes of device memory on first use.  Errors:
+ * EINVAL (NULL context), ENOMEM. */
+int ptycho_set_step_counter(ptycho_ctx* ctx, int64_t* t_dev);
 int ptycho_kernel_times(ptycho_ctx* ctx, const char** names, double* ms, int32_t* launches, int32_t cap);
 
 /* Self-test of failure detection on the device (N = 192, the tile whose

@@ -92,6 +92,7 @@ SIGNATURES = {
     "ptycho_check": (I32, [P_, P_]),
     "ptycho_make_groups": (I32, [I32, I32, C.c_uint64, C.c_int64, I32, P_, P_]),
     "ptycho_set_timing": (I32, [P_, I32]),
+    "ptycho_set_step_counter": (I32, [P_, P_]),
     "ptycho_kernel_times": (I32, [P_, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(I32), I32]),
     "ptycho_fft2": (I32, [I32, I32, P_, P_, I32, P_]),
     "ptycho_server_create": (I32, [C.c_size_t, I32, C.POINTER(P_)]),

@@ -247,6 +247,15 @@ class Context:
     def check_status(self):
         check(lib().ptycho_check(self.h, _stream()))
 
+    def set_step_counter(self, t):
+        """Keep the Adam step count in the int64 CUDA tensor t (one element,
+        ptycho_set_step_counter): steps captured in a CUDA graph then replay
+        with the right bias corrections.  None returns to the host count."""
+        if t is not None:
+            _need(t, torch.int64, (1,), "t")
+        check(lib().ptycho_set_step_counter(self.h, _ptr(t)))
+        self._t_dev = t
+
     def set_timing(self, on=True):
         check(lib().ptycho_set_timing(self.h, 1 if on else 0))
 

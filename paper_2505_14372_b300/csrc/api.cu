@@ -129,6 +129,10 @@ struct ptycho_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copied = nullptr;
   int split_B1 = 0;
+  // Adam step count in device memory (ptycho_set_step_counter) and the bias
+  // corrections of the current step
+  int64_t* t_dev = nullptr;
+  float* bc_dev = nullptr;
   // timing
   bool timing = false;
   struct Pending {
@@ -458,6 +462,7 @@ int ptycho_create(const ptycho_geom* geom, int32_t max_batch, size_t scratch_bud
 int ptycho_destroy(ptycho_ctx* c) {
   if (!c) return PTYCHO_OK;
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  cudaFree(c->bc_dev);
   if (c->copied) cudaEventDestroy(c->copied);
   for (auto& p : c->pending) {
     cudaEventDestroy(p.a);
@@ -599,11 +604,16 @@ static int step_impl(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
   const float bc2 = (float)(1.0 / (1.0 - std::pow((double)opt->beta2, (double)t)));
   {
     Timed tm(c, "adam", s);
+    const float* bcd = nullptr;
+    if (c->t_dev) {
+      CK(ptycho::launch_adam_count(reinterpret_cast<long long*>(c->t_dev), opt->beta1, opt->beta2, c->bc_dev, s));
+      bcd = c->bc_dev;
+    }
     CK(ptycho::launch_adam(reinterpret_cast<float2*>(O), reinterpret_cast<float2*>(st->mO), st->vO, c->gO, nO,
-                           opt->lr_O, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s));
+                           opt->lr_O, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s, bcd));
     if (opt->update_probe)
       CK(ptycho::launch_adam(reinterpret_cast<float2*>(P), reinterpret_cast<float2*>(st->mP), st->vP, c->gP, nP,
-                             opt->lr_P, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s));
+                             opt->lr_P, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s, bcd));
   }
   st->t = t;
   return PTYCHO_OK;
@@ -895,6 +905,20 @@ int ptycho_exchange_selftest(int32_t N) {
   CK(cudaDeviceSynchronize());
   if (ops->take_exchange_timeouts())
     return perr(PTYCHO_ETIMEDOUT, "the exchange wait gave up as the self-test expects");
+  return PTYCHO_OK;
+}
+
+int ptycho_set_step_counter(ptycho_ctx* c, int64_t* t_dev) {
+  int rc = check_call(c, 0);
+  if (rc) return rc;
+  if (t_dev && !c->bc_dev) {
+    if (cudaMalloc(&c->bc_dev, 2 * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      c->bc_dev = nullptr;
+      return perr(PTYCHO_ENOMEM, "no device memory for the bias corrections");
+    }
+  }
+  c->t_dev = t_dev;
   return PTYCHO_OK;
 }
 

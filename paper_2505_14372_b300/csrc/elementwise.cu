@@ -47,7 +47,11 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restri
 // z <- z - lr (m bc1) / (sqrt(v bc2) + eps), bc = 1/(1 - beta^t).
 __global__ void k_adam(float2* __restrict__ z, float2* __restrict__ m, float* __restrict__ v,
                        const float2* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                       float bc1, float bc2) {
+                       float bc1, float bc2, const float* __restrict__ bcd) {
+  if (bcd) {  // bias corrections of a step count kept in device memory
+    bc1 = bcd[0];
+    bc2 = bcd[1];
+  }
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const float2 gg = g[e];
     float2 mm = m[e];
@@ -173,11 +177,26 @@ cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out,
 }
 
 cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long long n, float lr, float b1,
-                        float b2, float eps, float bc1, float bc2, cudaStream_t s) {
+                        float b2, float eps, float bc1, float bc2, cudaStream_t s, const float* bcd) {
   if (n <= 0) return cudaSuccess;
   const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
   count_launch();
-  k_adam<<<blocks, 256, 0, s>>>(z, m, v, g, n, lr, b1, b2, eps, bc1, bc2);
+  k_adam<<<blocks, 256, 0, s>>>(z, m, v, g, n, lr, b1, b2, eps, bc1, bc2, bcd);
+  return cudaGetLastError();
+}
+
+// Adam step count in device memory (one thread): t <- t + 1 and the bias
+// corrections 1 / (1 - beta^t) of the new count, in FP64, into bc[2].
+__global__ void k_adam_count(long long* t, float b1, float b2, float* bc) {
+  const long long t1 = *t + 1;
+  bc[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t1)));
+  bc[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)t1)));
+  *t = t1;
+}
+
+cudaError_t launch_adam_count(long long* t, float b1, float b2, float* bc, cudaStream_t s) {
+  count_launch();
+  k_adam_count<<<1, 1, 0, s>>>(t, b1, b2, bc);
   return cudaGetLastError();
 }
 

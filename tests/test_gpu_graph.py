@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from gpu_util import dev, host, problem, rel_l2
-from paper_2505_14372_b300 import Context
+from paper_2505_14372_b300 import AdamState, Context, adam_opt
 
 pytestmark = pytest.mark.gpu
 
@@ -57,3 +57,42 @@ def test_forward_adjoint_capture_and_replay(N, S, K):
     # and the replay really used the new inputs
     first = host(ctx.forward(dev(O), dev(P), dev(pos)))
     assert rel_l2(replayed[0], first) > 1e-2
+
+
+def test_captured_step_replays_with_a_device_step_count():
+    """A whole Adam step (§3.2) captured once and replayed on successive
+    groups equals the same steps run eagerly, with the step count kept in
+    device memory (ptycho_set_step_counter)."""
+    N, S, K, B, n_pos = 64, 2, 2, 8, 24
+    geom, og, P, O, pos = problem(61, S, K, N, 112, 108, n_pos, loss="poisson", eps=0.8)
+    geom.waves = "recompute"
+    I_exp = np.random.default_rng(62).poisson(3.0, size=(n_pos, N, N)).astype(np.float32)
+    ctx = Context(geom, max_batch=B)
+    posd, Id = dev(pos), dev(I_exp)
+    opt = adam_opt(1e-2, 1e-3)
+    groups = [np.roll(np.arange(n_pos, dtype=np.int32), -5 * i)[:B].copy() for i in range(6)]
+
+    Oe, Pe, ste = dev(O), dev(P), AdamState(geom)
+    eager_loss = []
+    for gidx in groups:
+        eager_loss.append(float(ctx.step(Oe, Pe, ste, opt, posd, Id, dev(gidx))[0].item()))
+
+    t = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ctx.set_step_counter(t)
+    Og, Pg, stg = dev(O), dev(P), AdamState(geom)
+    idx = torch.empty(B, dtype=torch.int32, device="cuda")
+    stats = torch.zeros(2, dtype=torch.float64, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ctx.step(Og, Pg, stg, opt, posd, Id, idx, stats=stats)
+    replay_loss = []
+    for gidx in groups:
+        idx.copy_(dev(gidx))
+        graph.replay()
+        replay_loss.append(float(stats[0].item()))
+    torch.cuda.synchronize()
+    ctx.set_step_counter(None)
+    ctx.check_status()
+    assert int(t.item()) == len(groups)
+    assert np.allclose(replay_loss, eager_loss, rtol=1e-5)
+    assert rel_l2(host(Og), host(Oe)) < 1e-5 and rel_l2(host(Pg), host(Pe)) < 1e-5
