@@ -288,8 +288,12 @@ int ptycho_make_groups(int32_t P, int32_t B, uint64_t seed, int64_t iteration, i
 
 /* Per-kernel device time accumulated by this context's launches since the
  * last reset (CUDA events on the launching stream), enabled with
- * ptycho_set_timing(ctx, 1).  names/ms are host arrays of length cap;
- * returns the number of entries, or a negative code. */
+ * ptycho_set_timing(ctx, 1) for every kernel or ptycho_set_timing(ctx, 2)
+ * for the tile kernels (forward / adjoint) only, which keeps the events out
+ * of the short kernels of small problems.  Inside a stream capture the
+ * events are captured as external nodes, so each replay records its times.
+ * names/ms are host arrays of length cap; returns the number of entries, or
+ * a negative code. */
 int ptycho_set_timing(ptycho_ctx* ctx, int32_t enable);
 
 /* Adam step count kept in device memory, so that a step captured in a CUDA

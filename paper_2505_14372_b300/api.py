@@ -257,7 +257,8 @@ class Context:
         self._t_dev = t
 
     def set_timing(self, on=True):
-        check(lib().ptycho_set_timing(self.h, 1 if on else 0))
+        """on: True / 1 (every kernel), 2 (the tile kernels only), False / 0."""
+        check(lib().ptycho_set_timing(self.h, int(on)))
 
     def kernel_times(self, reset=False) -> dict:
         cap = 64

@@ -134,7 +134,7 @@ struct ptycho_ctx {
   int64_t* t_dev = nullptr;
   float* bc_dev = nullptr;
   // timing
-  bool timing = false;
+  int timing = 0;  // 0 off, 1 every kernel, 2 the tile kernels (forward / adjoint) only
   struct Pending {
     int kid;
     cudaEvent_t a, b;
@@ -169,6 +169,16 @@ cudaEvent_t take_event(ptycho_ctx* c) {
 }
 
 // Brackets one launch with CUDA events on its stream when timing is on.
+// Records a timing event on s; inside a stream capture as an external event
+// node, so that every replay of the graph records its time.
+void record_timing_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 struct Timed {
   ptycho_ctx* c;
   cudaStream_t s;
@@ -176,14 +186,15 @@ struct Timed {
   cudaEvent_t a = nullptr;
   Timed(ptycho_ctx* ctx, const char* name, cudaStream_t st) : c(ctx), s(st) {
     if (!c->timing) return;
+    if (c->timing == 2 && std::strcmp(name, "adjoint") != 0 && std::strcmp(name, "forward") != 0) return;
     kid = kernel_id(c, name);
     a = take_event(c);
-    cudaEventRecord(a, s);
+    record_timing_event(a, s);
   }
   ~Timed() {
     if (kid < 0) return;
     cudaEvent_t b = take_event(c);
-    cudaEventRecord(b, s);
+    record_timing_event(b, s);
     c->pending.push_back({kid, a, b});
   }
 };
@@ -854,7 +865,8 @@ int ptycho_check(ptycho_ctx* c, ptycho_stream stream) {
 
 int ptycho_set_timing(ptycho_ctx* c, int32_t enable) {
   if (!c) return perr(PTYCHO_EINVAL, "context is NULL");
-  c->timing = enable != 0;
+  if (enable < 0 || enable > 2) return perr(PTYCHO_EINVAL, "timing mode must be 0, 1 or 2");
+  c->timing = enable;
   return PTYCHO_OK;
 }
 
