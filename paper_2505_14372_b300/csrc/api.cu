@@ -604,27 +604,27 @@ static int step_impl(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
                                  opt->reg_obj_tikhonov, opt->reg_obj_layers, opt->reg_probe_l2, opt->reg_obj_tv,
                                  opt->reg_obj_layers_tv, opt->reg_tv_eps, partials + nl, nr, s));
   }
-  {
-    Timed t(c, "reduce", s);
-    CK(ptycho::launch_sumsq(c->gO, nO, partials + nl + nr, ptycho::kNormBlocks, s));
-    CK(ptycho::launch_sumsq(c->gP, nP, partials + nl + nr + ptycho::kNormBlocks, ptycho::kNormBlocks, s));
-    CK(ptycho::launch_finalize(partials, nl + nr, 2 * ptycho::kNormBlocks, stats, 1, s));
-  }
   const int64_t t = st->t + 1;
   const float bc1 = (float)(1.0 / (1.0 - std::pow((double)opt->beta1, (double)t)));
   const float bc2 = (float)(1.0 / (1.0 - std::pow((double)opt->beta2, (double)t)));
   {
+    // the Adam launches also write the |g|^2 partials of the gradients they read
     Timed tm(c, "adam", s);
     const float* bcd = nullptr;
     if (c->t_dev) {
       CK(ptycho::launch_adam_count(reinterpret_cast<long long*>(c->t_dev), opt->beta1, opt->beta2, c->bc_dev, s));
       bcd = c->bc_dev;
     }
+    double* normO = partials + nl + nr;
+    double* normP = normO + ptycho::kNormBlocks;
     CK(ptycho::launch_adam(reinterpret_cast<float2*>(O), reinterpret_cast<float2*>(st->mO), st->vO, c->gO, nO,
-                           opt->lr_O, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s, bcd));
+                           opt->lr_O, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s, bcd, normO));
     if (opt->update_probe)
       CK(ptycho::launch_adam(reinterpret_cast<float2*>(P), reinterpret_cast<float2*>(st->mP), st->vP, c->gP, nP,
-                             opt->lr_P, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s, bcd));
+                             opt->lr_P, opt->beta1, opt->beta2, opt->eps, bc1, bc2, s, bcd, normP));
+    else
+      CK(ptycho::launch_sumsq(c->gP, nP, normP, ptycho::kNormBlocks, s));
+    CK(ptycho::launch_finalize(partials, nl + nr, 2 * ptycho::kNormBlocks, stats, 1, s));
   }
   st->t = t;
   return PTYCHO_OK;
@@ -989,15 +989,20 @@ int finish_job(const StepJob& J, const Layout& L, int nl, cudaStream_t s) {
     CK(launch_regularize(J.O, c->gO, c->g.S, c->g.H, c->g.W, J.P, c->gP, nP, J.opt.reg_obj_l2, J.opt.reg_obj_tikhonov,
                          J.opt.reg_obj_layers, J.opt.reg_probe_l2, J.opt.reg_obj_tv, J.opt.reg_obj_layers_tv,
                          J.opt.reg_tv_eps, partials + nl, nr, s));
-  CK(launch_sumsq(c->gO, nO, partials + nl + nr, kNormBlocks, s));
-  CK(launch_sumsq(c->gP, nP, partials + nl + nr + kNormBlocks, kNormBlocks, s));
-  CK(launch_finalize(partials, nl + nr, 2 * kNormBlocks, J.stats, 1, s));
   const double t = (double)J.t;
   const float bc1 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta1, t)));
   const float bc2 = (float)(1.0 / (1.0 - std::pow((double)J.opt.beta2, t)));
-  CK(launch_adam(J.O, J.mO, J.vO, c->gO, nO, J.opt.lr_O, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s));
+  // the Adam launches also write the |g|^2 partials of the gradients they read
+  double* normO = partials + nl + nr;
+  double* normP = normO + kNormBlocks;
+  CK(launch_adam(J.O, J.mO, J.vO, c->gO, nO, J.opt.lr_O, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s, nullptr,
+                 normO));
   if (J.opt.update_probe)
-    CK(launch_adam(J.P, J.mP, J.vP, c->gP, nP, J.opt.lr_P, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s));
+    CK(launch_adam(J.P, J.mP, J.vP, c->gP, nP, J.opt.lr_P, J.opt.beta1, J.opt.beta2, J.opt.eps, bc1, bc2, s, nullptr,
+                   normP));
+  else
+    CK(launch_sumsq(c->gP, nP, normP, kNormBlocks, s));
+  CK(launch_finalize(partials, nl + nr, 2 * kNormBlocks, J.stats, 1, s));
   return PTYCHO_OK;
 }
 

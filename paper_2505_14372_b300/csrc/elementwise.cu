@@ -45,15 +45,22 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double* __restri
 
 // Complex Adam: m <- b1 m + (1-b1) g; v <- b2 v + (1-b2)|g|^2;
 // z <- z - lr (m bc1) / (sqrt(v bc2) + eps), bc = 1/(1 - beta^t).
-__global__ void k_adam(float2* __restrict__ z, float2* __restrict__ m, float* __restrict__ v,
-                       const float2* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                       float bc1, float bc2, const float* __restrict__ bcd) {
+// With `partials` the block also writes its FP64 partial of |g|^2 (the same
+// elements per block and order as k_sumsq on the same grid).
+__global__ void __launch_bounds__(kRedThreads) k_adam(float2* __restrict__ z, float2* __restrict__ m,
+                                                      float* __restrict__ v, const float2* __restrict__ g,
+                                                      long long n, float lr, float b1, float b2, float eps,
+                                                      float bc1, float bc2, const float* __restrict__ bcd,
+                                                      double* __restrict__ partials) {
+  __shared__ double sh[32];
   if (bcd) {  // bias corrections of a step count kept in device memory
     bc1 = bcd[0];
     bc2 = bcd[1];
   }
+  double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const float2 gg = g[e];
+    if (partials) acc += (double)gg.x * gg.x + (double)gg.y * gg.y;
     float2 mm = m[e];
     mm.x = fmaf(b1, mm.x, (1.0f - b1) * gg.x);
     mm.y = fmaf(b1, mm.y, (1.0f - b1) * gg.y);
@@ -66,6 +73,10 @@ __global__ void k_adam(float2* __restrict__ z, float2* __restrict__ m, float* __
     z[e] = zz;
     m[e] = mm;
     v[e] = vv;
+  }
+  if (partials) {
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
   }
 }
 
@@ -177,11 +188,12 @@ cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out,
 }
 
 cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long long n, float lr, float b1,
-                        float b2, float eps, float bc1, float bc2, cudaStream_t s, const float* bcd) {
-  if (n <= 0) return cudaSuccess;
-  const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+                        float b2, float eps, float bc1, float bc2, cudaStream_t s, const float* bcd,
+                        double* norm_partials) {
+  if (n <= 0 && !norm_partials) return cudaSuccess;
+  const int blocks = norm_partials ? kNormBlocks : (int)std::min<long long>((n + 255) / 256, 148LL * 16);
   count_launch();
-  k_adam<<<blocks, 256, 0, s>>>(z, m, v, g, n, lr, b1, b2, eps, bc1, bc2, bcd);
+  k_adam<<<blocks, kRedThreads, 0, s>>>(z, m, v, g, n, lr, b1, b2, eps, bc1, bc2, bcd, norm_partials);
   return cudaGetLastError();
 }
 

@@ -59,9 +59,11 @@ cudaError_t launch_finalize(const double* partials, int n0, int n1, double* out,
 cudaError_t launch_regularize(const float2* O, float2* gO, int S, int H, int W, const float2* P, float2* gP,
                               long long nP, float l2, float tik, float lay, float l2p, float tv, float tvl,
                               float eta, double* partials, int nblocks, cudaStream_t s);
-// bcd (device, optional): bias corrections written by launch_adam_count, used instead of bc1, bc2
+// bcd (device, optional): bias corrections written by launch_adam_count, used instead of bc1, bc2;
+// norm_partials (optional): kNormBlocks FP64 partials of |g|^2 (the update then runs on that grid)
 cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long long n, float lr, float b1,
-                        float b2, float eps, float bc1, float bc2, cudaStream_t s, const float* bcd = nullptr);
+                        float b2, float eps, float bc1, float bc2, cudaStream_t s, const float* bcd = nullptr,
+                        double* norm_partials = nullptr);
 cudaError_t launch_adam_count(long long* t, float b1, float b2, float* bc, cudaStream_t s);
 cudaError_t launch_slice_absmax(const float2* O, int S, long long per_slice, unsigned* omax, cudaStream_t s);
 cudaError_t launch_axpy(float2* z, const float2* g, long long n, float a, cudaStream_t s);
