@@ -41,7 +41,7 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3])
@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--dft", default="fft", choices=["fft", "tf32x3", "bf16x3", "tf32"],
                     help="DFT evaluation inside the tile (tensor-core variants: 192x192 window)")
-    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps)")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps, at most 10)")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: seeded Poisson arrivals of mixed-shape requests through ptycho_submit")
     ap.add_argument("--requests", type=int, default=64)
@@ -501,16 +501,20 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     k0 = kernels_launched()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one event between consecutive steps: the first and last bracket the
+    # timed region, the others give the per-step spread
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = evs[0], evs[-1]
     torch.cuda.synchronize()
     e0.record()
     for i in range(args.steps):
         one_step(args.warmup + i)
-    e1.record()
+        evs[i + 1].record()
     torch.cuda.synchronize()
     launches = kernels_launched() - k0 + graph_launches * args.steps
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
+    step_ms = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)])
     ctx.check_status()
     ktimes = ctx.kernel_times()
     ctx.set_timing(False)
@@ -524,10 +528,12 @@ def main():
     loss_last = stats.tolist()
 
     # ---- end to end through the C-ABI with host buffers (pinned), copies timed
-    e2e_steps = args.e2e_steps or args.steps
+    e2e_steps = args.e2e_steps or min(args.steps, 10)
     h_order = order[(args.warmup + args.steps) * B:][: e2e_steps * B]
     if len(h_order) < e2e_steps * B:
-        h_order = make_groups(wl.P, B, seed=99, iteration=0, mode="sparse")[: e2e_steps * B]
+        h_order = np.concatenate([make_groups(wl.P, B, seed=99, iteration=it, mode="sparse")
+                                  for it in range(math.ceil(e2e_steps * B / wl.P) + 1)])[: e2e_steps * B]
+    assert len(h_order) == e2e_steps * B, "every host-buffer step carries a full group"
     sel = torch.from_numpy(h_order.astype(np.int64)).to(dev)
     I_host = Iexp_d.index_select(0, sel).cpu().pin_memory()
     pos_host = pos_d.index_select(0, sel).cpu().pin_memory()
@@ -588,6 +594,11 @@ def main():
                 "ms_per_launch": dom_ms / dom_n,
                 "share_of_step": dom_ms / ms,
                 "kernels_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()}}
+    if traffic is not None:
+        # the same kernel against the HBM roof: its DRAM bytes (ncu) over its live launch time
+        gbs = traffic / (dom_ms / dom_n / 1e3) / 1e9
+        roofline["dram"] = {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": gbs / peaks["hbm_gbs"], "peak_source": f"{peak_src} copy bandwidth"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "positions/s", "n_gpus": world, "steps": args.steps,
@@ -597,6 +608,8 @@ def main():
                                **({"graph": "one captured step replayed per step"} if graph_launches else {}),
                                **({"loss": "amplitude"} if args.engine in ("epie", "lsqml") else {}),
                                **({"positions_used": wl.P} if args.positions else {})),
+                "step_ms": {"median": float(np.median(step_ms)), "p99": float(np.percentile(step_ms, 99)),
+                            "min": float(step_ms.min()), "max": float(step_ms.max()), "n": int(args.steps)},
                 "roofline": roofline, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "last_stats": loss_last}
         if world == 1 and not args.no_baseline:
