@@ -191,3 +191,24 @@ def test_step_with_regularizers_parity(reg):
                                  I_exp, idx, og, 1e-2, 1e-3, reg=reg)
     assert abs(stats[0] - L) < TOL_MS * abs(L) and abs(stats[1] - gn) < TOL_MS * gn
     assert rel_l2(host(Od), O2) < 1e-5 and rel_l2(host(Pd), P2) < 1e-5
+
+
+@pytest.mark.parametrize("N,S,K,H,W", [(64, 2, 2, 84, 84), (192, 2, 2, 200, 200)])
+def test_step_with_fixed_probe_parity(N, S, K, H, W):
+    """A step that keeps the probe fixed (§3.2 with only the object among the
+    optimised variables): the object moves as the oracle's, the probe does
+    not, and the reported gradient norm still covers the probe gradient."""
+    geom, og, P, O, pos = problem(75 + N, S, K, N, H, W, 6, loss="poisson", eps=0.8)
+    I_exp = np.random.default_rng(9).poisson(orc.forward(O, P, pos, og) + 0.5).astype(np.float32)
+    idx = np.array([5, 2, 0, 3], np.int32)
+    ctx = Context(geom, max_batch=4)
+    Od, Pd = dev(O), dev(P)
+    st = AdamState(geom)
+    stats = host(ctx.step(Od, Pd, st, adam_opt(lr_O=1e-2, lr_P=1e-2, update_probe=False), dev(pos), dev(I_exp),
+                          dev(idx)))
+    z = np.zeros
+    O2, P2, *_, L, gn = orc.step(O, P, z(O.shape, complex), z(O.shape), z(P.shape, complex), z(P.shape), 1, pos,
+                                 I_exp, idx, og, 1e-2, 1e-2, update_probe=False)
+    assert np.array_equal(host(Pd), P.astype(np.complex64))
+    assert abs(stats[0] - L) < TOL_MS * abs(L) and abs(stats[1] - gn) < TOL_MS * gn
+    assert rel_l2(host(Od), O2) < 1e-5
