@@ -26,12 +26,20 @@ namespace ptycho {
 // branch-free.
 template <int PREC>
 __device__ __forceinline__ void wave_put(char* base, int i, float2 v) {
+  // streaming stores: the entry waves are read back once, after every mode's
+  // forward pass, so they should not displace the object patch in L2
   if constexpr (PREC == 0) {
-    reinterpret_cast<float2*>(base)[i] = v;
-  } else if constexpr (PREC == 1) {
-    reinterpret_cast<__half2*>(base)[i] = __floats2half2_rn(v.x, v.y);
+    __stcs(reinterpret_cast<float2*>(base) + i, v);
   } else {
-    reinterpret_cast<__nv_bfloat162*>(base)[i] = __floats2bfloat162_rn(v.x, v.y);
+    unsigned u;
+    if constexpr (PREC == 1) {
+      const __half2 h = __floats2half2_rn(v.x, v.y);
+      memcpy(&u, &h, sizeof(u));
+    } else {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+      memcpy(&u, &h, sizeof(u));
+    }
+    __stcs(reinterpret_cast<unsigned*>(base) + i, u);
   }
 }
 template <int PREC>
