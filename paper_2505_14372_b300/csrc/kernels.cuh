@@ -191,10 +191,13 @@ struct PropOp {
   const int* fsq;
   int blT;
   __device__ void operator()(int pu, int pv, float2& v) const {
-    const bool keep = blT < 0 || fsq[pu] + fsq[pv] <= blT;
-    const float2 hh = cmul(h[pu], h[pv]);
-    const float s = keep ? 1.0f / (float)TL::NP : 0.0f;
-    v = CONJ ? cscale(cmulc(v, hh), s) : cscale(cmul(v, hh), s);
+    // fsq of the row slot from its index (no table read); the column
+    // factor h[pv] / NP is common to a column task's slots
+    const int fu = TL::freq(TL::nat(pu));
+    const bool keep = blT < 0 || fu * fu + fsq[pv] <= blT;
+    const float2 hh = cmul(h[pu], cscale(h[pv], 1.0f / (float)TL::NP));
+    const float2 w = CONJ ? cmulc(v, hh) : cmul(v, hh);
+    v = keep ? w : make_float2(0.f, 0.f);
   }
 };
 
