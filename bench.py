@@ -193,6 +193,18 @@ def adjoint_algorithmic_flops(wl, items, recompute):
     return items * (ffts * fft_flops(NP) + prods * 6.0 * NP)
 
 
+def host_buffer_order(order, used_groups, steps, P, B):
+    """Positions of the host-buffer leg: the groups after the `used_groups`
+    of the device-timed leg, else fresh passes; every step a full group of B."""
+    from paper_2505_14372_b300 import make_groups
+    h = order[used_groups * B:][: steps * B]
+    if len(h) < steps * B:
+        h = np.concatenate([make_groups(P, B, seed=99, iteration=it, mode="sparse")
+                            for it in range(math.ceil(steps * B / P) + 1)])[: steps * B]
+    assert len(h) == steps * B, "every host-buffer step carries a full group"
+    return h
+
+
 def cpu_oracle_leg(wl, geom, pos_all_np, n_pos_sample, O_init, P_np, sample_note, min_seconds=10.0, max_steps=200):
     """Times the FP64 oracle's steps on a bounded sample of the workload:
     consecutive steps of n_pos_sample positions each, until about
@@ -529,11 +541,7 @@ def main():
 
     # ---- end to end through the C-ABI with host buffers (pinned), copies timed
     e2e_steps = args.e2e_steps or min(args.steps, 10)
-    h_order = order[(args.warmup + args.steps) * B:][: e2e_steps * B]
-    if len(h_order) < e2e_steps * B:
-        h_order = np.concatenate([make_groups(wl.P, B, seed=99, iteration=it, mode="sparse")
-                                  for it in range(math.ceil(e2e_steps * B / wl.P) + 1)])[: e2e_steps * B]
-    assert len(h_order) == e2e_steps * B, "every host-buffer step carries a full group"
+    h_order = host_buffer_order(order, args.warmup + args.steps, e2e_steps, wl.P, B)
     sel = torch.from_numpy(h_order.astype(np.int64)).to(dev)
     I_host = Iexp_d.index_select(0, sel).cpu().pin_memory()
     pos_host = pos_d.index_select(0, sel).cpu().pin_memory()
