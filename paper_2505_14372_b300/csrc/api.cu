@@ -24,7 +24,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Offsets of one call's scratch inside the context arena.
 struct Layout {
-  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, omax, wmax, waves, pA, pI, total;
+  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, order, omax, wmax, waves, pA, pI, total;
 };
 
 Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
@@ -47,6 +47,7 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   L.stats = take(4 * 8);
   L.stage_pos = take((size_t)B * 2 * 4);
   L.stage_I = take((size_t)B * NP * 4);
+  L.order = take((size_t)B * 4);  // processing order of a position-major launch
   L.omax = take((size_t)g.S * 4);
   L.wmax = take((size_t)B * g.K * g.S * 4);
   const size_t esize = g.wave_prec ? 4 : 8;  // entry-wave copies: complex64 or two 16-bit parts
@@ -320,7 +321,8 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   const int variant = epie ? ptycho::kVarEpie : c->g.wave_prec;
   if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
   if (!c->store && !vjp && c->pos_clusters > 0) {
-    const ptycho::PosArgs F = pos_args(c, L);
+    ptycho::PosArgs F = pos_args(c, L);
+    int* order = reinterpret_cast<int*>(c->arena + L.order);
     set_pos_loss(d, Iexp, partials, model, c->g);
     CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
     // split: positions [0, B1) first, then the rest once their patterns
@@ -330,6 +332,8 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
       LaunchArgs la = one_position_problem(c, L, d);
       la.d[0].B = B1;
       la.total = B1;
+      CK(ptycho::launch_locality_order(la, order, s));
+      F.order = order;
       Timed t(c, "adjoint", s);
       CK(c->ops->adjoint_pos(la, F, std::min(B1, c->pos_clusters), variant, s));
     }
@@ -341,6 +345,8 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
       d2.B = B - B1;
       d2.npos = B - B1;
       LaunchArgs la2 = one_position_problem(c, L, d2);
+      CK(ptycho::launch_locality_order(la2, order + B1, s));
+      F.order = order + B1;
       CK(cudaStreamWaitEvent(s, c->copied, 0));
       Timed t(c, "adjoint", s);
       CK(c->ops->adjoint_pos(la2, F, std::min(B - B1, c->pos_clusters), variant, s));
@@ -794,6 +800,9 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
   d.lsq_il = il;
   set_pos_loss(d, I_exp_all, partials, ptycho::kModelEpie, c->g);  // the modulus-update seed
   LaunchArgs la = one_position_problem(c, L, d);
+  // both passes take the group's positions in the same locality order
+  CK(ptycho::launch_locality_order(la, reinterpret_cast<int*>(c->arena + L.order), s));
+  F.order = reinterpret_cast<const int*>(c->arena + L.order);
   {
     Timed t(c, "adjoint", s);
     CK(c->ops->adjoint_pos(la, F, clusters, ptycho::kVarLsqDir, s));

@@ -206,6 +206,59 @@ __global__ void k_adam_count(long long* t, float b1, float b2, float* bc) {
   *t = t1;
 }
 
+// Processing order of a position-major launch.  The clusters running at one
+// time take consecutive entries of the order, so sorting the positions along
+// a Morton curve of their window origins makes those clusters read
+// neighbouring, overlapping object patches, which then serve each other
+// from L2.  Rank sort (stable: ties by position index), one thread per
+// position against tiles of keys in shared memory.
+__device__ __forceinline__ unsigned spread_bits16(unsigned v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+__device__ unsigned long long locality_key(const LaunchArgs& L, int it) {
+  int d = 0;
+  while (d + 1 < L.nd && it >= L.d[d + 1].item0) ++d;
+  const ProblemDesc& D = L.d[d];
+  const int j = it - D.item0;
+  const int jj = D.idx ? D.idx[j] : j;
+  unsigned y = 0, x = 0;
+  if (jj >= 0 && jj < D.npos) {  // out-of-range positions are flagged by the kernel itself
+    y = (unsigned)fminf(fmaxf(D.pos[2 * (size_t)jj], 0.f), 65535.f);
+    x = (unsigned)fminf(fmaxf(D.pos[2 * (size_t)jj + 1], 0.f), 65535.f);
+  }
+  return ((unsigned long long)d << 32) | (spread_bits16(y) << 1) | spread_bits16(x);
+}
+__global__ void __launch_bounds__(kRedThreads) k_locality_order(const __grid_constant__ LaunchArgs L, int* order) {
+  __shared__ unsigned long long tile[kRedThreads];
+  const int it = blockIdx.x * kRedThreads + threadIdx.x;
+  const bool mine = it < L.total;
+  const unsigned long long key = mine ? locality_key(L, it) : 0ull;
+  int rank = 0;
+  for (int base = 0; base < L.total; base += kRedThreads) {
+    const int i = base + threadIdx.x;
+    tile[threadIdx.x] = i < L.total ? locality_key(L, i) : ~0ull;
+    __syncthreads();
+    const int n = min(kRedThreads, L.total - base);
+    for (int q = 0; q < n; ++q) {
+      const unsigned long long kq = tile[q];
+      rank += (kq < key || (kq == key && base + q < it)) ? 1 : 0;
+    }
+    __syncthreads();
+  }
+  if (mine) order[rank] = it;
+}
+cudaError_t launch_locality_order(const LaunchArgs& L, int* order, cudaStream_t s) {
+  if (L.total <= 0) return cudaSuccess;
+  count_launch();
+  k_locality_order<<<(L.total + kRedThreads - 1) / kRedThreads, kRedThreads, 0, s>>>(L, order);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_adam_count(long long* t, float b1, float b2, float* bc, cudaStream_t s) {
   count_launch();
   k_adam_count<<<1, 1, 0, s>>>(t, b1, b2, bc);

@@ -484,7 +484,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
   float2* Ab = F.Abuf + (size_t)cid * F.astride;
   float* Ib = F.Ibuf + (size_t)cid * TL::NP;
 #pragma unroll 1
-  for (int jg = cid; jg < L.total; jg += n_clusters<TL>()) {
+  for (int it = cid; it < L.total; it += n_clusters<TL>()) {
+    const int jg = F.order ? __ldg(F.order + it) : it;
     // position j of problem D (item0: its first position in the launch)
     const ProblemDesc& D = find_desc(L, jg);
     const int j = jg - D.item0;

@@ -80,6 +80,10 @@ struct PosArgs {
   float* Ibuf;         // [clusters][NP] mode-summed intensity, then 2 l'(I) / NP
   long long astride;   // float2 per cluster in Abuf (>= K NP of every problem)
   float gamma;         // LSQML step-size regulariser
+  // processing order [total]: a permutation of the launch's positions (the
+  // clusters take order[cid], order[cid + clusters], ...), or null for
+  // 0, 1, ...; outputs stay indexed by position
+  const int* order;
 };
 
 }  // namespace ptycho
