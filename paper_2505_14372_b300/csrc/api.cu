@@ -321,7 +321,7 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   const int variant = epie ? ptycho::kVarEpie : c->g.wave_prec;
   if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
   if (!c->store && !vjp && c->pos_clusters > 0) {
-    const ptycho::PosArgs F = pos_args(c, L);
+    ptycho::PosArgs F = pos_args(c, L);
     int* order = reinterpret_cast<int*>(c->arena + L.order);
     set_pos_loss(d, Iexp, partials, model, c->g);
     CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
@@ -333,7 +333,7 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
       la.d[0].B = B1;
       la.total = B1;
       CK(ptycho::launch_locality_order(la, order, s));
-      la.d[0].order = order;
+      F.order = order;
       Timed t(c, "adjoint", s);
       CK(c->ops->adjoint_pos(la, F, std::min(B1, c->pos_clusters), variant, s));
     }
@@ -346,7 +346,7 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
       d2.npos = B - B1;
       LaunchArgs la2 = one_position_problem(c, L, d2);
       CK(ptycho::launch_locality_order(la2, order + B1, s));
-      la2.d[0].order = order + B1;
+      F.order = order + B1;
       CK(cudaStreamWaitEvent(s, c->copied, 0));
       Timed t(c, "adjoint", s);
       CK(c->ops->adjoint_pos(la2, F, std::min(B - B1, c->pos_clusters), variant, s));
@@ -801,9 +801,8 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
   set_pos_loss(d, I_exp_all, partials, ptycho::kModelEpie, c->g);  // the modulus-update seed
   LaunchArgs la = one_position_problem(c, L, d);
   // both passes take the group's positions in the same locality order
-  int* order = reinterpret_cast<int*>(c->arena + L.order);
-  CK(ptycho::launch_locality_order(la, order, s));
-  la.d[0].order = order;
+  CK(ptycho::launch_locality_order(la, reinterpret_cast<int*>(c->arena + L.order), s));
+  F.order = reinterpret_cast<const int*>(c->arena + L.order);
   {
     Timed t(c, "adjoint", s);
     CK(c->ops->adjoint_pos(la, F, clusters, ptycho::kVarLsqDir, s));
@@ -843,7 +842,6 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
   d2.lsq_numP = numP;
   d2.lsq_denP = denP;
   d2.lsq_aw = aw;
-  d2.order = order;
   LaunchArgs la2 = one_position_problem(c, L, d2);
   CK(cudaMemsetAsync(d2.lpart, 0, (size_t)B * 8, s));
   {
@@ -1038,12 +1036,8 @@ int step_batch_pos(const StepJob* jobs, int n, const PosScratch& ps, unsigned* s
     CK(cudaMemsetAsync(partials, 0, (size_t)J.B * 8, s));
     ProblemDesc d = base_desc(c, L[i], reinterpret_cast<const ptycho_c64*>(J.O), J.pos, J.idx, J.B, J.n_pos);
     d.gO = c->gO;
-    set_pos_loss(d, J.Iexp, partials, c->g.loss, c->g);
-    // the job's processing order, in its own context's scratch
-    int* order = reinterpret_cast<int*>(c->arena + L[i].order);
-    CK(launch_locality_order(one_position_problem(c, L[i], d), order, s));
-    d.order = order;
     d.item0 = total;
+    set_pos_loss(d, J.Iexp, partials, c->g.loss, c->g);
     total += J.B;
     la.d[i] = d;
   }

@@ -485,10 +485,10 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
   float* Ib = F.Ibuf + (size_t)cid * TL::NP;
 #pragma unroll 1
   for (int it = cid; it < L.total; it += n_clusters<TL>()) {
-    // position j of problem D (item0: its first slot in the launch), taken
-    // in the problem's processing order
-    const ProblemDesc& D = find_desc(L, it);
-    const int j = D.order ? __ldg(D.order + (it - D.item0)) : it - D.item0;
+    const int jg = F.order ? __ldg(F.order + it) : it;
+    // position j of problem D (item0: its first position in the launch)
+    const ProblemDesc& D = find_desc(L, jg);
+    const int j = jg - D.item0;
     const int K = D.K;
     // one mode's entry waves (and, in the LSQML step pass, its shifted probe direction)
     const size_t wstride = (size_t)(D.S + Var<V>::extra_waves) * TL::NP * Var<V>::wave_bytes;

@@ -36,10 +36,6 @@ struct ProblemDesc {
   int npos;             // rows of pos (and of the pattern array) idx may select
   int blT;              // band limit keeps f_u^2 + f_v^2 <= blT; < 0: off
   int item0;            // first global item (position-major kernel: position) of this problem
-  // position-major kernel: processing order [B], a permutation of the
-  // problem's positions (its launch slots item0 + i take positions
-  // order[i]), or null for 0, 1, ...; outputs stay indexed by position
-  const int* order;
   // position-major loss + adjoint: measured patterns [npos][NP] (natural
   // order), loss per position [B] (zeroed per launch) and the noise model
   const float* Iexp;
@@ -84,6 +80,10 @@ struct PosArgs {
   float* Ibuf;         // [clusters][NP] mode-summed intensity, then 2 l'(I) / NP
   long long astride;   // float2 per cluster in Abuf (>= K NP of every problem)
   float gamma;         // LSQML step-size regulariser
+  // processing order [total]: a permutation of the launch's positions (the
+  // clusters take order[cid], order[cid + clusters], ...), or null for
+  // 0, 1, ...; outputs stay indexed by position
+  const int* order;
 };
 
 }  // namespace ptycho
