@@ -208,18 +208,10 @@ __global__ void k_adam_count(long long* t, float b1, float b2, float* bc) {
 
 // Processing order of a position-major launch.  The clusters running at one
 // time take consecutive entries of the order, so sorting the positions along
-// a Morton curve of their window origins makes those clusters read
+// a Hilbert curve of their window origins makes those clusters read
 // neighbouring, overlapping object patches, which then serve each other
 // from L2.  Rank sort (stable: ties by position index), one thread per
 // position against tiles of keys in shared memory.
-__device__ __forceinline__ unsigned spread_bits16(unsigned v) {
-  v &= 0xffffu;
-  v = (v | (v << 8)) & 0x00ff00ffu;
-  v = (v | (v << 4)) & 0x0f0f0f0fu;
-  v = (v | (v << 2)) & 0x33333333u;
-  v = (v | (v << 1)) & 0x55555555u;
-  return v;
-}
 __device__ unsigned long long locality_key(const LaunchArgs& L, int it) {
   int d = 0;
   while (d + 1 < L.nd && it >= L.d[d + 1].item0) ++d;
@@ -231,7 +223,22 @@ __device__ unsigned long long locality_key(const LaunchArgs& L, int it) {
     y = (unsigned)fminf(fmaxf(D.pos[2 * (size_t)jj], 0.f), 65535.f);
     x = (unsigned)fminf(fmaxf(D.pos[2 * (size_t)jj + 1], 0.f), 65535.f);
   }
-  return ((unsigned long long)d << 32) | (spread_bits16(y) << 1) | spread_bits16(x);
+  // index along a Hilbert curve of order 16 (no jumps between neighbours)
+  unsigned h = 0;
+  for (unsigned sq = 1u << 15; sq > 0; sq >>= 1) {
+    const unsigned ry = (y & sq) ? 1u : 0u, rx = (x & sq) ? 1u : 0u;
+    h += sq * sq * ((3u * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = 0xffffu - x;
+        y = 0xffffu - y;
+      }
+      const unsigned t = x;
+      x = y;
+      y = t;
+    }
+  }
+  return ((unsigned long long)d << 32) | h;
 }
 __global__ void __launch_bounds__(kRedThreads) k_locality_order(const __grid_constant__ LaunchArgs L, int* order) {
   __shared__ unsigned long long tile[kRedThreads];

@@ -65,8 +65,8 @@ cudaError_t launch_adam(float2* z, float2* m, float* v, const float2* g, long lo
                         float b2, float eps, float bc1, float bc2, cudaStream_t s, const float* bcd = nullptr,
                         double* norm_partials = nullptr);
 cudaError_t launch_adam_count(long long* t, float b1, float b2, float* bc, cudaStream_t s);
-// order[0, L.total): the launch's positions sorted by (problem, Morton code of
-// the window origin), the processing order of the position-major kernel
+// order[0, L.total): the launch's positions sorted by (problem, Hilbert index
+// of the window origin), the processing order of the position-major kernel
 cudaError_t launch_locality_order(const LaunchArgs& L, int* order, cudaStream_t s);
 cudaError_t launch_slice_absmax(const float2* O, int S, long long per_slice, unsigned* omax, cudaStream_t s);
 cudaError_t launch_axpy(float2* z, const float2* g, long long n, float a, cudaStream_t s);
