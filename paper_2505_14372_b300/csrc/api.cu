@@ -965,9 +965,11 @@ int resident_slots(int N) {
   return ops ? ops->resident_clusters(true, false, kVarF32) : 0;
 }
 
+// positions of one served launch that get a processing order
+constexpr int kOrderCap = kMaxDesc * 4096;
 size_t pos_scratch_bytes(int N, int kmodes, int smax) {
   const size_t NP = (size_t)N * N, cl = (size_t)resident_slots(N);
-  return cl * ((size_t)kmodes * (smax + 1) * NP * 8 + (size_t)kmodes * NP * 8 + NP * 4);
+  return cl * ((size_t)kmodes * (smax + 1) * NP * 8 + (size_t)kmodes * NP * 8 + NP * 4) + (size_t)kOrderCap * 4;
 }
 PosScratch pos_scratch_at(char* base, int N, int kmodes, int smax) {
   PosScratch p;
@@ -979,6 +981,8 @@ PosScratch pos_scratch_at(char* base, int N, int kmodes, int smax) {
   p.slots = base;
   p.A = reinterpret_cast<float2*>(base + (size_t)p.clusters * p.slot_bytes);
   p.I = reinterpret_cast<float*>(reinterpret_cast<char*>(p.A) + (size_t)p.clusters * kmodes * NP * 8);
+  p.order = reinterpret_cast<int*>(p.I + (size_t)p.clusters * NP);
+  p.order_cap = kOrderCap;
   return p;
 }
 
@@ -1046,6 +1050,10 @@ int step_batch_pos(const StepJob* jobs, int n, const PosScratch& ps, unsigned* s
   F.Abuf = ps.A;
   F.Ibuf = ps.I;
   F.astride = (long long)ps.kmodes * jobs[0].c->NP;
+  if (ps.order && total <= ps.order_cap) {  // each job's positions along a Hilbert curve
+    CK(launch_locality_order(la, ps.order, s));
+    F.order = ps.order;
+  }
   CK(ops->adjoint_pos(la, F, std::min(total, ps.clusters), kVarF32, s));
   for (int i = 0; i < n; ++i) {
     const int rc = finish_job(jobs[i], L[i], jobs[i].B, s);

@@ -37,7 +37,8 @@ struct PosScratch {
   long long slot_bytes = 0;
   float2* A = nullptr;       // [clusters][kmodes NP]
   float* I = nullptr;        // [clusters][NP]
-  int clusters = 0, kmodes = 0, smax = 0;
+  int* order = nullptr;      // [order_cap] processing order of a launch's positions
+  int clusters = 0, kmodes = 0, smax = 0, order_cap = 0;
 };
 // Bytes of a PosScratch for window N (clusters = resident_slots(N)).
 size_t pos_scratch_bytes(int N, int kmodes, int smax);
