@@ -249,6 +249,13 @@ LaunchArgs one_position_problem(ptycho_ctx* c, const Layout& L, const ProblemDes
   a.slot_stride = (long long)c->g.K * (c->g.S + 1) * c->NP * (c->g.wave_prec ? 4 : 8);
   return a;
 }
+// A processing order pays only when the object does not sit in L2 anyway
+// (then the clusters running at one time must share their patches there);
+// below this size the extra launch would cost more than it saves.
+constexpr size_t kOrderMinObjectBytes = 64ull << 20;
+bool order_pays(size_t object_bytes) { return object_bytes > kOrderMinObjectBytes; }
+size_t object_bytes(const ptycho_ctx* c) { return (size_t)c->g.S * c->g.H * c->g.W * 8; }
+
 ptycho::PosArgs pos_args(ptycho_ctx* c, const Layout& L) {
   ptycho::PosArgs F{};
   F.Abuf = reinterpret_cast<float2*>(c->arena + L.pA);
@@ -332,8 +339,10 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
       LaunchArgs la = one_position_problem(c, L, d);
       la.d[0].B = B1;
       la.total = B1;
-      CK(ptycho::launch_locality_order(la, order, s));
-      F.order = order;
+      if (order_pays(object_bytes(c))) {
+        CK(ptycho::launch_locality_order(la, order, s));
+        F.order = order;
+      }
       Timed t(c, "adjoint", s);
       CK(c->ops->adjoint_pos(la, F, std::min(B1, c->pos_clusters), variant, s));
     }
@@ -345,8 +354,10 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
       d2.B = B - B1;
       d2.npos = B - B1;
       LaunchArgs la2 = one_position_problem(c, L, d2);
-      CK(ptycho::launch_locality_order(la2, order + B1, s));
-      F.order = order + B1;
+      if (order_pays(object_bytes(c))) {
+        CK(ptycho::launch_locality_order(la2, order + B1, s));
+        F.order = order + B1;
+      }
       CK(cudaStreamWaitEvent(s, c->copied, 0));
       Timed t(c, "adjoint", s);
       CK(c->ops->adjoint_pos(la2, F, std::min(B - B1, c->pos_clusters), variant, s));
@@ -801,8 +812,10 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
   set_pos_loss(d, I_exp_all, partials, ptycho::kModelEpie, c->g);  // the modulus-update seed
   LaunchArgs la = one_position_problem(c, L, d);
   // both passes take the group's positions in the same locality order
-  CK(ptycho::launch_locality_order(la, reinterpret_cast<int*>(c->arena + L.order), s));
-  F.order = reinterpret_cast<const int*>(c->arena + L.order);
+  if (order_pays(object_bytes(c))) {
+    CK(ptycho::launch_locality_order(la, reinterpret_cast<int*>(c->arena + L.order), s));
+    F.order = reinterpret_cast<const int*>(c->arena + L.order);
+  }
   {
     Timed t(c, "adjoint", s);
     CK(c->ops->adjoint_pos(la, F, clusters, ptycho::kVarLsqDir, s));
@@ -1050,7 +1063,9 @@ int step_batch_pos(const StepJob* jobs, int n, const PosScratch& ps, unsigned* s
   F.Abuf = ps.A;
   F.Ibuf = ps.I;
   F.astride = (long long)ps.kmodes * jobs[0].c->NP;
-  if (ps.order && total <= ps.order_cap) {  // each job's positions along a Hilbert curve
+  size_t objects = 0;
+  for (int i = 0; i < n; ++i) objects += object_bytes(jobs[i].c);
+  if (ps.order && total <= ps.order_cap && order_pays(objects)) {  // each job's positions along a Hilbert curve
     CK(launch_locality_order(la, ps.order, s));
     F.order = ps.order;
   }
