@@ -369,6 +369,11 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
   }
   LaunchArgs la = one_problem(c, L, d);
   const int items = B * K;
+  if (order_pays(object_bytes(c))) {  // positions along a Hilbert curve, as in the position-major step
+    int* order = reinterpret_cast<int*>(c->arena + L.order);
+    CK(ptycho::launch_locality_order(one_position_problem(c, L, d), order, s));
+    la.order = order;
+  }
   {
     Timed t(c, "forward", s);
     CK(c->ops->forward(la, std::min(items, c->res_fwd), c->store, variant, s));
@@ -534,6 +539,11 @@ int ptycho_forward(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, cons
   ProblemDesc d = base_desc(c, L, O, pos, nullptr, B, B);
   d.waves = nullptr;
   LaunchArgs la = one_problem(c, L, d);
+  if (order_pays(object_bytes(c))) {
+    int* order = reinterpret_cast<int*>(c->arena + L.order);
+    CK(ptycho::launch_locality_order(one_position_problem(c, L, d), order, s));
+    la.order = order;
+  }
   {
     Timed t(c, "forward", s);
     CK(c->ops->forward(la, std::min(B * c->g.K, c->res_fwd), false, ptycho::kVarF32, s));

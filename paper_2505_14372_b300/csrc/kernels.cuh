@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_forward(const __grid_consta
   TL::init_tables(sm.twS, sm.twC, sm.fsq);
   constexpr int N = TL::N;
 #pragma unroll 1
-  for (int item = cluster_id<TL>(); item < L.total; item += n_clusters<TL>()) {
+  for (int it = cluster_id<TL>(); it < L.total; it += n_clusters<TL>()) {
+    const int item = L.order ? __ldg(L.order + it / L.d[0].K) * L.d[0].K + it % L.d[0].K : it;
     // the partner CTAs must be done with the previous item before remote
     // writes of this one can land in their exchange buffers
     TL::sync_cluster();
@@ -422,7 +423,8 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_consta
   TL::init_tables(sm.twS, sm.twC, sm.fsq);
   constexpr int N = TL::N;
 #pragma unroll 1
-  for (int item = cluster_id<TL>(); item < L.total; item += n_clusters<TL>()) {
+  for (int it = cluster_id<TL>(); it < L.total; it += n_clusters<TL>()) {
+    const int item = L.order ? __ldg(L.order + it / L.d[0].K) * L.d[0].K + it % L.d[0].K : it;
     // the partner CTAs must be done with the previous item before remote
     // writes of this one can land in their exchange buffers
     TL::sync_cluster();

@@ -67,6 +67,10 @@ struct LaunchArgs {
   unsigned* status;         // device status word (PTYCHO_STATUS_*)
   char* slots;              // recompute scratch, one slot per cluster
   long long slot_stride;    // bytes per slot
+  // item-major kernels, one-problem launches: processing order of the
+  // positions ([B], a permutation; the items of position order[p] are taken
+  // at p K .. p K + K - 1), or null for item order
+  const int* order;
 };
 
 // Extra arguments of the position-major loss + adjoint kernel: one cluster
