@@ -311,6 +311,80 @@ def test_step_reduces_loss_on_consistent_data():
     assert losses[-1] < 0.5 * losses[0]
 
 
+def _adam_closed(z, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    # Adam's moment recursion and bias corrections written out per element
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * (g.real ** 2 + g.imag ** 2)
+    return z - lr * (m / (1.0 - b1 ** t)) / (np.sqrt(v / (1.0 - b2 ** t)) + eps), m, v
+
+
+def test_step_gnorm_holds_regularizer_gradient_and_step_count():
+    """The step's gradient norm, loss and Adam step count (§3.2, §3.4), on a
+    case whose gradient is known in closed form: with a zero probe the
+    wavefield, the patterns and the data term's gradient vanish for ANY
+    object (amplitude loss, I = I_exp = 0), so the whole gradient is the
+    object-L2 regulariser's 2 lam (O - 1) and the loss its lam sum |O - 1|^2.
+    Two steps at t = 1, 2 must reproduce Adam written out by hand: the first
+    moves every element by exactly lr along (O - 1) / |O - 1| (bias
+    correction of t = 1); the second sees the new gradient 2 lam (O1 - 1).
+    Fails if the regulariser is left out of the norm or of the update, or if
+    the step count is passed off by one."""
+    g = tiny(S=2, K=2, loss=orc.AMPLITUDE, eps=1e-3)
+    O = phase_obj(2, 12, 12) * (0.7 + 0.6 * RNG.random((2, 12, 12)))
+    P = np.zeros((2, 8, 8), complex)
+    E = np.zeros((4, 8, 8))
+    lam, lr = 0.05, 0.01
+    zO, zP = np.zeros_like(O), np.zeros(O.shape)
+    mP, vP = np.zeros_like(P), np.zeros(P.shape)
+    O1, P1, mO, vO, mP1, vP1, loss, gn = orc.step(O, P, zO, zP, mP, vP, 1, POS4, E, np.arange(4), g,
+                                                   lr, 0.02, reg={"l2_obj": lam})
+    d = O - 1.0
+    assert math.isclose(loss, lam * float(np.sum(np.abs(d) ** 2)), rel_tol=1e-12)
+    assert math.isclose(gn, 2 * lam * float(np.sqrt(np.sum(np.abs(d) ** 2))), rel_tol=1e-12)
+    # first step: m_hat = g, v_hat = |g|^2, so the move is lr g / (|g| + eps)
+    gO0 = 2 * lam * d
+    assert np.allclose(O - O1, lr * gO0 / (np.abs(gO0) + 1e-8), rtol=1e-12, atol=1e-15)
+    assert np.array_equal(P1, P)  # zero probe gradient: no move
+    O2, _, _, _, _, _, loss2, gn2 = orc.step(O1, P1, mO, vO, mP1, vP1, 2, POS4, E, np.arange(4), g,
+                                             lr, 0.02, reg={"l2_obj": lam})
+    gO1 = 2 * lam * (O1 - 1.0)
+    assert math.isclose(gn2, float(np.sqrt(np.sum(np.abs(gO1) ** 2))), rel_tol=1e-12)
+    assert math.isclose(loss2, lam * float(np.sum(np.abs(O1 - 1.0) ** 2)), rel_tol=1e-12)
+    zc, mc, vc = _adam_closed(O, np.zeros_like(O), np.zeros(O.shape), gO0, 1, lr)
+    zc, mc, vc = _adam_closed(zc, mc, vc, gO1, 2, lr)
+    assert np.allclose(O2, zc, rtol=1e-12, atol=1e-15)
+    # an off-by-one step count moves the second step measurably
+    zw, _, _ = _adam_closed(O1, mc * 0 + (1 - 0.9) * gO0, (1 - 0.999) * np.abs(gO0) ** 2, gO1, 3, lr)
+    assert np.max(np.abs(zw - zc)) > 1e-4 * lr
+
+
+def test_step_gnorm_holds_probe_gradient():
+    """At data simulated from the current object and probe, the amplitude
+    loss and its gradient vanish (§3.1), so with the probe-L2 regulariser
+    alone the step's gradient is g_P = 2 lam P (closed form) and g_O = 0:
+    the norm is 2 lam |P|, the loss lam |P|^2, the object stays put and the
+    probe takes Adam's first step lr g / |g|.  With the probe held fixed the
+    norm still counts g_P.  Fails if g_P is dropped from the norm."""
+    g = tiny(S=2, K=2, loss=orc.AMPLITUDE, eps=1e-3)
+    O = phase_obj(2, 12, 12)
+    P = crand(2, 8, 8, scale=2.0)
+    E = orc.forward(O, P, POS4, g)
+    lam, lr = 0.03, 0.02
+    for upd in (True, False):
+        O1, P1, *_, loss, gn = orc.step(O, P, np.zeros_like(O), np.zeros(O.shape), np.zeros_like(P),
+                                       np.zeros(P.shape), 1, POS4, E, np.arange(4), g, 0.01, lr,
+                                       update_probe=upd, reg={"l2_probe": lam})
+        nP = float(np.sqrt(np.sum(np.abs(P) ** 2)))
+        assert math.isclose(gn, 2 * lam * nP, rel_tol=1e-9)
+        assert math.isclose(loss, lam * nP ** 2, rel_tol=1e-9)
+        assert np.allclose(O1, O, rtol=0, atol=1e-12)
+        if upd:
+            gP = 2 * lam * P
+            assert np.allclose(P - P1, lr * gP / (np.abs(gP) + 1e-8), rtol=1e-8, atol=1e-12)
+        else:
+            assert np.array_equal(P1, P)
+
+
 def test_gradient_fd_on_four_position_multislice_subproblem():
     """Directional finite differences of the full 20-slice, 8-mode, 192x192
     problem on four neighbouring scan positions (the workload's gradient
