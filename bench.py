@@ -36,6 +36,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+adjoint probe-positions/s (multislice, mixed-state); p50/p99 serve latency"
 FP32_LANES_PER_SM = 128
+# what the geometry's waves modes mean for the step: "recompute" runs the
+# forward pass inside the adjoint kernel and keeps every slice's entry wave of
+# the positions in flight in per-cluster HBM slots (4S 2-D FFTs per mode, no
+# slice recomputed twice); "store" keeps the whole group's entry waves
+WAVES_LABEL = {"recompute": "slot-stored (forward inside the adjoint kernel; entry waves of the positions in "
+                            "flight in per-cluster HBM slots)",
+               "store": "stored (the whole group's entry waves from a separate forward launch)"}
 
 
 def parse():
@@ -142,7 +149,7 @@ def workload_geometry(wl, waves, dft="fft", wave_prec="f32"):
 def config_dict(wl, waves, dft="fft", wave_prec="f32"):
     return {"workload": wl.name, "dft": dft, "wave_storage": wave_prec, "slices": wl.S, "modes": wl.K, "window": wl.N, "object": [wl.H, wl.W],
             "positions": wl.P, "group": wl.B, "loss": {0: "amplitude", 1: "poisson"}[wl.loss],
-            "waves": waves, "grouping": "sparse, reshuffled every pass",
+            "waves": WAVES_LABEL.get(waves, waves), "grouping": "sparse, reshuffled every pass",
             "l2": "inputs larger than L2 (patterns %.1f GB, object %.0f MB) - no flush" % (
                 wl.P * wl.N * wl.N * 4 / 1e9, wl.S * wl.H * wl.W * 8 / 1e6)}
 
@@ -510,6 +517,14 @@ def main():
         def one_step(i):  # noqa: F811 - the replayed step
             idx_buf.copy_(group(i))
             graph.replay()
+    # FP32 CUDA-core peak of this GPU (FFMA / FFMA2 microbenchmark), with
+    # the SM clock it ran at: the denominator of the tile kernel's roofline
+    from paper_2505_14372_b300.api import fp32_peak
+    psamp = ClockSampler(local)
+    psamp.start()
+    peak_meas = fp32_peak()
+    peak_meas["clocks"] = psamp.stop()
+    torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
     k0 = kernels_launched()
@@ -584,7 +599,8 @@ def main():
     else:
         flops = B * wl.K * 2 * wl.S * fft_flops(wl.N * wl.N)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_tf = nsm * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    nominal_tf = nsm * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    peak_tf = peak_meas["tflops"]
     achieved = flops / (dom_ms / dom_n / 1e3) / 1e12
     traffic_path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     traffic = None
@@ -597,8 +613,16 @@ def main():
             traffic = tj[key]["bytes_per_item"] * B * wl.K
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved / peak_tf, "traffic": traffic,
-                "peak_source": f"FP32 CUDA cores: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{peaks.get('sm_max_mhz', 2032.0):.0f} MHz ({peak_src} max SM clock)",
+                "peak_source": "measured: FP32 FFMA/FFMA2 microbenchmark on this GPU just before the timed "
+                               "region (ptycho_fp32_peak_launch, best of 3 launches of ~0.3 s, CUDA events)",
+                "peak_measurement": {"ffma_tflops": peak_meas["ffma"]["tflops"],
+                                     "ffma2_tflops": peak_meas["ffma2"]["tflops"],
+                                     "sm_mhz": peak_meas["clocks"].get("sm_mhz"),
+                                     "reasons": peak_meas["clocks"].get("reasons")},
+                "frac_of_nominal": achieved / nominal_tf,
+                "nominal_peak": nominal_tf,
+                "nominal_source": f"{nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                  f"{peaks.get('sm_max_mhz', 2032.0):.0f} MHz ({peak_src} max SM clock)",
                 "ms_per_launch": dom_ms / dom_n,
                 "share_of_step": dom_ms / ms,
                 "kernels_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()}}

@@ -378,3 +378,37 @@ def kernels_launched() -> int:
 
 def version() -> str:
     return lib().ptycho_version().decode()
+
+
+def fp32_peak(target_ms: float = 300.0, repeats: int = 3) -> dict:
+    """Measured FP32 CUDA-core throughput of the current device (TFLOP/s):
+    the library's FFMA and FFMA2 microbenchmark kernels, each launched
+    `repeats` times at about target_ms per launch after one warm-up launch,
+    timed with CUDA events on the current stream; the best launch of each."""
+    sink = torch.empty(int(lib().ptycho_fp32_peak_sink_elems()), dtype=torch.float32, device="cuda")
+    flops = C.c_double(0.0)
+    out = {}
+    for packed, name in ((0, "ffma"), (1, "ffma2")):
+        iters = 256
+        # warm-up, then size the launch to about target_ms
+        check(lib().ptycho_fp32_peak_launch(packed, iters, _ptr(sink), C.byref(flops), _stream()))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        check(lib().ptycho_fp32_peak_launch(packed, iters, _ptr(sink), C.byref(flops), _stream()))
+        e1.record()
+        torch.cuda.synchronize()
+        iters = max(1, int(iters * target_ms / max(e0.elapsed_time(e1), 1e-3)))
+        best = 0.0
+        ms_best = None
+        for _ in range(repeats):
+            e0.record()
+            check(lib().ptycho_fp32_peak_launch(packed, iters, _ptr(sink), C.byref(flops), _stream()))
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            tf = flops.value / (ms / 1e3) / 1e12
+            if tf > best:
+                best, ms_best = tf, ms
+        out[name] = {"tflops": best, "ms": ms_best, "iters": iters}
+    out["tflops"] = max(out["ffma"]["tflops"], out["ffma2"]["tflops"])
+    return out
