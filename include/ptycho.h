@@ -60,6 +60,8 @@ extern "C" {
 #define PTYCHO_ETIMEDOUT (-5)    /* a bounded wait ran out */
 #define PTYCHO_EBUSY (-6)        /* request not finished / server busy */
 #define PTYCHO_ENOTFOUND (-7)    /* unknown ticket */
+/* bits of a device status word (ptycho_forward_static's status_out) */
+#define PTYCHO_STATUS_BIT_OUT_OF_BOUNDS 1u /* a scan window left the object; its item was skipped */
 
 typedef struct {
   float re, im;
@@ -164,20 +166,29 @@ int ptycho_vjp(ptycho_ctx* ctx, const ptycho_c64* O, const ptycho_c64* P, const 
  * memory to its own pool, a plug-in whose host forbids allocating).  The
  * paper has no counterpart: it is a packaging of ptycho_forward.
  * Computes the same I_out[B][N][N] as ptycho_forward for the geometry *geom
- * (copied per call; no context), using the kernels of ptycho_forward and a
- * fixed 32 MiB scratch array that lives in the library (every GPU that loads
- * the library holds it until exit).  The problem must fit it:
- * K*N*N*8*(B+1) + (S-1)*N*8 plus a little alignment <= 32 MiB, else EINVAL
- * with the sizes in the message.  Calls no cudaMalloc or cudaFree.  The first
- * call on each device resolves the array's device address
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture.  All calls share the array and it keeps the
- * last call's contents; each call clears what must start at zero.  Calls
- * whose work overlaps on the GPU (other streams, other host threads) race on
- * the shared scratch: order them.  Positions outside the object give zero
- * intensity for their pattern. */
+ * (checked like ptycho_create's and read per call; no context), using the
+ * kernels of ptycho_forward and a fixed 32 MiB scratch array that lives in
+ * the library (every GPU that loads the library holds it until exit).  The
+ * problem must fit it: K*N*N*8*(B+1) + (S-1)*N*8 plus a little alignment
+ * <= 32 MiB, and S <= 65 (the slice gaps travel in the kernel's arguments),
+ * else EINVAL with the sizes in the message.  Calls no cudaMalloc or
+ * cudaFree and copies nothing from host memory; the array's device address
+ * is resolved once per CUDA context (cudaGetSymbolAddress with that context
+ * current) on the first call made in it, so make that first call before any
+ * stream capture; the tensor-core DFT modes (geom->dft != 0) also fill their
+ * constant tables on their first use on a device (a synchronous copy, no
+ * allocation).  All calls share the array and it keeps the last call's
+ * contents; each call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the
+ * shared scratch: order them.  Positions outside the object give zero
+ * intensity for their pattern and set PTYCHO_STATUS_BIT_OUT_OF_BOUNDS in
+ * the call's status word, which is copied (stream-ordered) to *status_out
+ * when status_out (a device uint32) is not NULL.  A bounded exchange wait
+ * of the 192 x 192 tile that runs out (a partner CTA that never answers;
+ * not expected in practice) raises the library-wide time-out flag that the
+ * next ptycho_check of any 192 x 192 context reports as ETIMEDOUT. */
 int ptycho_forward_static(const ptycho_geom* geom, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
-                          int32_t B, float* I_out, ptycho_stream stream);
+                          int32_t B, float* I_out, uint32_t* status_out, ptycho_stream stream);
 
 /* Adam hyper-parameters (§3.2; Optax-style defaults 0.9, 0.999, 1e-8) and
  * the weights of the cost regularisers added to the loss (§3.4; 0 = off):
@@ -392,6 +403,21 @@ int ptycho_poll(ptycho_server* srv, uint64_t ticket, ptycho_status* st, ptycho_r
 int ptycho_wait(ptycho_server* srv, uint64_t ticket, double timeout_ms);
 int ptycho_release(ptycho_server* srv, uint64_t ticket);
 int ptycho_server_stats_get(ptycho_server* srv, ptycho_server_stats* out);
+
+/* FP32 CUDA-core throughput microbenchmark (measurement support: the
+ * denominator of the roofline of the FFT tile kernels, whose arithmetic is
+ * FP32 on the CUDA cores; the paper has no counterpart).  Enqueues ONE
+ * kernel on `stream`: 8 blocks of 256 threads per SM, each thread running
+ * 16 independent x <- x*a + b chains for iters x 16 rounds, as scalar FFMA
+ * (packed = 0) or packed two-wide FFMA2 (packed != 0).  *flops_out (host)
+ * receives the FP32 flops the launch performs (2 per FMA); the caller times
+ * the launch on the stream (CUDA events) and divides.  sink: device float
+ * array of ptycho_fp32_peak_sink_elems() elements (never written in
+ * practice; keeps the chains live).  EINVAL for iters < 1 or NULL
+ * pointers, ECUDA if the launch fails. */
+int ptycho_fp32_peak_launch(int32_t packed, int32_t iters, float* sink, double* flops_out,
+                            ptycho_stream stream);
+int32_t ptycho_fp32_peak_sink_elems(void);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * contexts and servers); a diagnostic for counting device work. */

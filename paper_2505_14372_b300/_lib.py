@@ -82,7 +82,7 @@ SIGNATURES = {
     "ptycho_adjoint": (I32, [P_, P_, P_, P_, I32, P_, P_, P_, P_, I32, P_]),
     "ptycho_vjp": (I32, [P_, P_, P_, P_, I32, P_, P_, P_, I32, P_]),
     "ptycho_adjoint_positions": (I32, [P_, P_, P_, P_, I32, P_, P_, P_, P_, P_, I32, P_]),
-    "ptycho_forward_static": (I32, [C.POINTER(Geom), P_, P_, P_, I32, P_, P_]),
+    "ptycho_forward_static": (I32, [C.POINTER(Geom), P_, P_, P_, I32, P_, P_, P_]),
     "ptycho_step": (I32, [P_, P_, P_, C.POINTER(Adam), C.POINTER(Opt), P_, P_, I32, P_, I32, P_, P_]),
     "ptycho_step_host": (I32, [P_, P_, P_, C.POINTER(Adam), C.POINTER(Opt), P_, P_, I32,
                                C.POINTER(C.c_double), C.POINTER(C.c_double), P_]),
@@ -102,6 +102,8 @@ SIGNATURES = {
     "ptycho_wait": (I32, [P_, C.c_uint64, C.c_double]),
     "ptycho_release": (I32, [P_, C.c_uint64]),
     "ptycho_server_stats_get": (I32, [P_, C.POINTER(ServerStats)]),
+    "ptycho_fp32_peak_launch": (I32, [I32, I32, P_, C.POINTER(C.c_double), P_]),
+    "ptycho_fp32_peak_sink_elems": (I32, []),
     "ptycho_kernels_launched": (C.c_uint64, []),
     "ptycho_last_error": (C.c_char_p, []),
     "ptycho_version": (C.c_char_p, []),

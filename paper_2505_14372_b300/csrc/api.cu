@@ -61,7 +61,11 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   return L;
 }
 
-int validate_geom(const ptycho_geom* g) {
+}  // namespace
+
+// Host checks of a geometry shared by every entry point that takes one
+// (internal.h).
+int ptycho::validate_geom(const ptycho_geom* g) {
   if (!g) return perr(PTYCHO_EINVAL, "geometry is NULL");
   if (g->S < 1 || g->K < 1) return perr(PTYCHO_EINVAL, "need S >= 1 and K >= 1");
   if (g->h != g->w) return perr(PTYCHO_EINVAL, "window must be square (h == w)");
@@ -92,6 +96,9 @@ int validate_geom(const ptycho_geom* g) {
   if (cells > 4.0e9) return perr(PTYCHO_EINVAL, "object too large");
   return PTYCHO_OK;
 }
+
+namespace {
+using ptycho::validate_geom;
 
 // Band-limit threshold on f_u^2 + f_v^2 (square window): the grid keeps
 // (f_u w)^2 + (f_v h)^2 <= floor(x*x) with x = beta*h*w*0.5 in IEEE double.

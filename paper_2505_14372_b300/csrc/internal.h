@@ -9,6 +9,11 @@
 
 namespace ptycho {
 
+// Host checks of a geometry (dimensions, window size, DFT mode, physics
+// parameters, noise model, waves mode, storage format, object size);
+// PTYCHO_OK or PTYCHO_EINVAL with the thread-local message set.
+int validate_geom(const ptycho_geom* g);
+
 // One problem's gradient step inside a batched launch (device pointers).
 struct StepJob {
   ptycho_ctx* c;

@@ -9,13 +9,15 @@
 // tables are cudaMalloc'd.  This entry point needs no context.  Its scratch
 // (probe spectra, far fields, the propagator chirp and a status word) lives
 // in one file-scope __device__ array of fixed size, and the caller passes
-// only inputs and outputs.
+// only inputs and outputs (and, optionally, a device word for the status).
 //
 // The array is a property of the loaded library: every GPU that loads it
 // holds kStaticScratchBytes until the process exits.  All calls on a device
 // share it, so calls whose work overlaps on the GPU (different streams, or
 // different host threads) race on it; callers must order them.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -24,52 +26,112 @@
 
 #include "engine.h"
 #include "errors.h"
+#include "internal.h"
 #include "launch.h"
 #include "ptycho.h"
 
 namespace {
 
 constexpr size_t kStaticScratchBytes = 32u << 20;  // 32 MiB
-constexpr int kMaxDevices = 64;
+constexpr int kMaxStaticGaps = 64;                 // S <= 65 slices
+constexpr int kAddrCache = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Device address of g_static_scratch per device, resolved once per device
-// (cudaGetSymbolAddress with that device current): in host code the array's
-// name is only a stand-in, not a device address.
-void* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
+// Device address of g_static_scratch per CUDA context.  In host code the
+// array's name is only a stand-in, not a device address; a __device__ array
+// exists once per context (a non-primary context on the same device, or the
+// primary context re-created after cudaDeviceReset, holds its own copy), so
+// the address is resolved with cudaGetSymbolAddress once per context, with
+// that context current, and cached under the context's unique id
+// (cuCtxGetId, never reused within a process).
+struct AddrEntry {
+  unsigned long long ctx_id;
+  void* addr;
+};
+AddrEntry g_addr[kAddrCache] = {};
+int g_addr_next = 0;
+std::mutex g_addr_mu;
+PFN_cuCtxGetCurrent_v4000 g_get_current = nullptr;
+PFN_cuCtxGetId_v12000 g_get_id = nullptr;
 
-int scratch_address(int dev, void** out) {
-  if (dev < 0 || dev >= kMaxDevices) return perr(PTYCHO_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return perr(PTYCHO_ECUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
-                                    cudaGetErrorString(e));
-    }
-    g_scratch_addr[dev] = p;
+int driver_entry_points() {
+  if (g_get_current && g_get_id) return PTYCHO_OK;
+  cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
+  void* f1 = nullptr;
+  void* f2 = nullptr;
+  const cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1);
+  const cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+      q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+    cudaGetLastError();
+    return perr(PTYCHO_ECUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not available");
   }
-  *out = g_scratch_addr[dev];
+  g_get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+  g_get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+  return PTYCHO_OK;
+}
+
+int resolve_symbol(void** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return perr(PTYCHO_ECUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
+                                  cudaGetErrorString(e));
+  }
+  *out = p;
+  return PTYCHO_OK;
+}
+
+// Address of the scratch in the current context (resolving it, and making
+// the runtime bind its primary context, on the context's first call).
+int scratch_address(void** out) {
+  std::lock_guard<std::mutex> lk(g_addr_mu);
+  int rc = driver_entry_points();
+  if (rc) return rc;
+  CUcontext ctx = nullptr;
+  if (g_get_current(&ctx) != CUDA_SUCCESS) return perr(PTYCHO_ECUDA, "cuCtxGetCurrent failed");
+  void* fresh = nullptr;
+  if (!ctx) {
+    // no context bound yet: the runtime binds the device's primary context
+    // while resolving the symbol
+    if ((rc = resolve_symbol(&fresh))) return rc;
+    if (g_get_current(&ctx) != CUDA_SUCCESS || !ctx) return perr(PTYCHO_ECUDA, "no current CUDA context");
+  }
+  unsigned long long id = 0;
+  if (g_get_id(ctx, &id) != CUDA_SUCCESS) return perr(PTYCHO_ECUDA, "cuCtxGetId failed");
+  for (const AddrEntry& a : g_addr)
+    if (a.addr && a.ctx_id == id) {
+      *out = a.addr;
+      return PTYCHO_OK;
+    }
+  if (!fresh && (rc = resolve_symbol(&fresh))) return rc;
+  g_addr[g_addr_next] = {id, fresh};
+  g_addr_next = (g_addr_next + 1) % kAddrCache;
+  *out = fresh;
   return PTYCHO_OK;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// The slice gaps travel by value in the kernel's parameters, so a call copies
+// nothing from host memory.
+struct Gaps {
+  double dz[kMaxStaticGaps];
+};
+
 // Separable Fresnel chirp per gap in spectral slot order (the same table
 // ptycho_create builds on the host): phase in turns formed and reduced in
 // FP64 before the sincos.
-__global__ void k_static_chirp_table(float2* Hc, const double* dz_dev, int gaps, int N, int R1, int R2, double lam,
-                                     double dx) {
+__global__ void k_static_chirp_table(float2* Hc, const __grid_constant__ Gaps gaps, int ngaps, int N, int R1, int R2,
+                                     double lam, double dx) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= gaps * N) return;
+  if (i >= ngaps * N) return;
   const int s = i / N, p = i % N;
   const int n = p / R2 + R1 * (p % R2);
   const double f = n < (N + 1) / 2 ? n : n - N;
-  double t = lam * dz_dev[s] * f * f / (2.0 * (double)N * N * dx * dx);
+  double t = lam * gaps.dz[s] * f * f / (2.0 * (double)N * N * dx * dx);
   t -= rint(t);
   double sn, cs;
   sincospi(-2.0 * t, &sn, &cs);
@@ -79,21 +141,20 @@ __global__ void k_static_chirp_table(float2* Hc, const double* dz_dev, int gaps,
 }  // namespace
 
 extern "C" int ptycho_forward_static(const ptycho_geom* g, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
-                                     int32_t B, float* I_out, ptycho_stream stream) {
-  if (!g) return perr(PTYCHO_EINVAL, "geometry is NULL");
+                                     int32_t B, float* I_out, uint32_t* status_out, ptycho_stream stream) {
+  int rc = ptycho::validate_geom(g);
+  if (rc) return rc;
+  if (g->S - 1 > kMaxStaticGaps)
+    return perr(PTYCHO_EINVAL, "ptycho_forward_static takes at most " + std::to_string(kMaxStaticGaps + 1) +
+                                   " slices (use ptycho_forward with a context instead)");
   const ptycho::EngineOps* ops = ptycho::engine_for(g->h, g->dft);
-  if (!ops || g->h != g->w) return perr(PTYCHO_EINVAL, "window must be square with N in {64, 128, 192, 256}");
-  if (g->S < 1 || g->K < 1 || g->H < g->h || g->W < g->w || !(g->dx > 0) || !(g->lambda > 0) ||
-      (g->S > 1 && !g->dz))
-    return perr(PTYCHO_EINVAL, "bad geometry");
   if (B < 0) return perr(PTYCHO_EINVAL, "B < 0");
   if (B == 0) return PTYCHO_OK;
   if (!O || !P || !pos || !I_out) return perr(PTYCHO_EINVAL, "NULL array argument");
   const int N = g->h, K = g->K, S = g->S;
   const size_t NP = (size_t)N * N;
-  // scratch layout: status | dz (FP64) | chirp | probe spectra | far fields
-  const size_t off_dz = 256;
-  const size_t off_hc = off_dz + align256((size_t)std::max(S - 1, 1) * 8);
+  // scratch layout: status | chirp | probe spectra | far fields
+  const size_t off_hc = 256;
   const size_t off_ph = off_hc + align256((size_t)std::max(S - 1, 1) * N * 8);
   const size_t off_a = off_ph + align256((size_t)K * NP * 8);
   const size_t need = off_a + align256((size_t)B * K * NP * 8);
@@ -101,14 +162,8 @@ extern "C" int ptycho_forward_static(const ptycho_geom* g, const ptycho_c64* O, 
     return perr(PTYCHO_EINVAL, "problem needs " + std::to_string(need) + " bytes of scratch; the static scratch of "
                                    "ptycho_forward_static holds " + std::to_string(kStaticScratchBytes) +
                                    " (use ptycho_forward with a context instead)");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return perr(PTYCHO_ECUDA, "no CUDA device");
-  }
   void* base = nullptr;
-  int rc = scratch_address(dev, &base);
-  if (rc) return rc;
+  if ((rc = scratch_address(&base))) return rc;
   unsigned char* sc = static_cast<unsigned char*>(base);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned* status = reinterpret_cast<unsigned*>(sc);
@@ -123,13 +178,10 @@ extern "C" int ptycho_forward_static(const ptycho_geom* g, const ptycho_c64* O, 
     return perr(PTYCHO_ECUDA, "cudaMemsetAsync failed");
   }
   if (S > 1) {
-    if (cudaMemcpyAsync(sc + off_dz, g->dz, (size_t)(S - 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-      cudaGetLastError();
-      return perr(PTYCHO_ECUDA, "copy of the slice gaps failed");
-    }
+    Gaps gaps{};
+    for (int i = 0; i + 1 < S; ++i) gaps.dz[i] = g->dz[i];
     const int n = (S - 1) * N;
-    k_static_chirp_table<<<(n + 255) / 256, 256, 0, s>>>(Hc, reinterpret_cast<const double*>(sc + off_dz), S - 1, N,
-                                                          ops->R1, ops->R2, g->lambda, g->dx);
+    k_static_chirp_table<<<(n + 255) / 256, 256, 0, s>>>(Hc, gaps, S - 1, N, ops->R1, ops->R2, g->lambda, g->dx);
     ptycho::count_launch();
   }
   int blT = -1;
@@ -162,6 +214,7 @@ extern "C" int ptycho_forward_static(const ptycho_geom* g, const ptycho_c64* O, 
                      ptycho::kVarF32, s);
   }
   if (e == cudaSuccess) e = ops->modesum(A, I_out, B, K, s);
+  if (e == cudaSuccess && status_out) e = cudaMemcpyAsync(status_out, status, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return perr(PTYCHO_ECUDA, std::string("forward launch failed: ") + cudaGetErrorString(e));

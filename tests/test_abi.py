@@ -106,3 +106,24 @@ def test_reduced_precision_halves_store_scratch():
     half = scratch_bytes(geom, 64, "store")
     waves = 64 * 2 * 5 * 64 * 64 * 8
     assert full - half == pytest.approx(waves / 2, abs=512)
+
+
+def test_static_forward_host_validation():
+    """ptycho_forward_static rejects bad geometry, too many slices and
+    problems larger than its fixed scratch on the host, before any device
+    work (so these need no GPU)."""
+    lib = _lib.lib()
+    fake = C.c_void_p(16)  # never dereferenced: every case fails validation first
+
+    def call(geom, B=4):
+        g, _dz = geom.to_c()
+        return lib.ptycho_forward_static(C.byref(g), fake, fake, fake, B, fake, None, None)
+
+    assert call(Geometry(S=1, K=1, N=100, H=128, W=128)) == _lib.EINVAL
+    assert call(Geometry(S=2, K=1, N=64, H=80, W=80, dz=(float("nan"),))) == _lib.EINVAL
+    assert call(Geometry(S=70, K=1, N=64, H=80, W=80, dz=(10.0,) * 69)) == _lib.EINVAL
+    assert b"at most 65 slices" in lib.ptycho_last_error()
+    assert call(Geometry(S=1, K=8, N=256, H=300, W=300), B=64) == _lib.EINVAL
+    assert b"static scratch" in lib.ptycho_last_error()
+    assert call(Geometry(S=1, K=1, N=64, H=80, W=80), B=-1) == _lib.EINVAL
+    assert call(Geometry(S=1, K=1, N=64, H=80, W=80), B=0) == _lib.OK
