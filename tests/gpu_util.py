@@ -34,7 +34,7 @@ def problem(seed, S, K, N, H, W, B, loss="amplitude", eps=1e-3, c=0.0, bandlimit
     geom = Geometry(S=S, K=K, N=N, H=H, W=W, dx=0.1, lam=0.0197, dz=tuple([dz] * (S - 1)),
                     bandlimit=bandlimit, loss=loss, eps=eps, c=c)
     og = orc.Geom(S=S, K=K, h=N, w=N, H=H, W=W, dx=0.1, lam=0.0197, dz=geom.dz, bandlimit=bandlimit,
-                  loss={"amplitude": 0, "poisson": 1}[loss], eps=eps, c=c)
+                  loss={"amplitude": 0, "anscombe": 0, "poisson": 1}[loss], eps=eps, c=c)
     return geom, og, P.astype(np.complex64), O.astype(np.complex64), pos
 
 

@@ -34,6 +34,9 @@ CASES = [
     (192, 1, 2, 200, 210, 5, "amplitude"),
     (192, 3, 2, 200, 200, 3, "poisson"),
     (256, 2, 1, 260, 270, 3, "amplitude"),
+    # the multislice workload's depth and modes (20 slices, 8 modes, 192 x 192)
+    # on a reduced object, element by element
+    (192, 20, 8, 230, 230, 4, "poisson"),
 ]
 
 
@@ -65,6 +68,23 @@ def test_adjoint_parity(N, S, K, H, W, B, loss, waves):
     ctx.check_status()
     L, rO, rP = orc.gradient(O, P, pos, I_exp, og)
     assert abs(float(loss_d.item()) - L) <= _tol(S) * abs(L)
+    assert rel_l2(host(gO), rO) < TOL_MS
+    assert rel_l2(host(gP), rP) < TOL_MS
+
+
+@pytest.mark.parametrize("waves", ["store", "recompute"])
+@pytest.mark.parametrize("N,S,K,H,W,B", [(64, 2, 2, 90, 84, 9), (192, 2, 2, 200, 206, 3)])
+def test_adjoint_parity_anscombe(N, S, K, H, W, B, waves):
+    """The Anscombe noise model (§3.1: least squares on sqrt(I + 3/8)),
+    loss and gradients against the oracle."""
+    geom, og, P, O, pos = problem(N * 13 + S, S, K, N, H, W, B, loss="anscombe", eps=1e-3, c=0.375, edge=True)
+    geom.waves = waves
+    I_exp = np.random.default_rng(15).poisson(orc.forward(O, P, pos, og) * 1.1 + 0.2).astype(np.float32)
+    ctx = Context(geom, max_batch=B)
+    loss_d, gO, gP = ctx.adjoint(dev(O), dev(P), dev(pos), dev(I_exp))
+    ctx.check_status()
+    L, rO, rP = orc.gradient(O, P, pos, I_exp, og)
+    assert abs(float(loss_d.item()) - L) <= TOL_MS * abs(L)
     assert rel_l2(host(gO), rO) < TOL_MS
     assert rel_l2(host(gP), rP) < TOL_MS
 

@@ -88,6 +88,47 @@ def test_results_equal_alone_and_in_the_mix():
     srv.close()
 
 
+def oracle_trajectory(geom, P, pos, I_exp, iters, batch, seed, lr_O, lr_P):
+    """The FP64 oracle's steps over the groups the server forms (the same
+    seeded grouping), from a vacuum object and the request's probe."""
+    og = orc.Geom(S=geom.S, K=geom.K, h=geom.N, w=geom.N, H=geom.H, W=geom.W, dx=geom.dx, lam=geom.lam,
+                  dz=geom.dz, bandlimit=geom.bandlimit, loss={"amplitude": 0, "poisson": 1}[geom.loss],
+                  eps=geom.eps, c=geom.c)
+    O = np.ones((geom.S, geom.H, geom.W), np.complex128)
+    Pc = P.astype(np.complex128)
+    mO, vO, mP, vP = np.zeros_like(O), np.zeros(O.shape), np.zeros_like(Pc), np.zeros(Pc.shape)
+    t, losses = 0, []
+    for it in range(iters):
+        perm = make_groups(len(pos), batch, seed=seed, iteration=it, mode="sparse")
+        for g0 in range(0, len(pos), batch):
+            t += 1
+            O, Pc, mO, vO, mP, vP, L, _ = orc.step(O, Pc, mO, vO, mP, vP, t, pos, I_exp, perm[g0:g0 + batch], og,
+                                                   lr_O, lr_P)
+            losses.append(L)
+    return O, Pc, np.array(losses)
+
+
+def test_served_results_match_the_oracle_in_the_mix():
+    """Two requests of different window sizes served together (their steps
+    share launches): each result follows the FP64 oracle's trajectory over
+    the same groups (loss of every step, final object and probe)."""
+    picks = [0, 3]
+    reqs = [request(**REQS[i]) for i in picks]
+    srv = Server(16 * GB, 4)
+    tickets = [srv.submit(r[0], r[2], r[3], r[1], iterations=2, batch=8, seed=13, opt=adam_opt(1e-2, 1e-3))
+               for r in reqs]
+    for t in tickets:
+        srv.wait(t)
+    for r, t in zip(reqs, tickets):
+        o = srv.poll(t, r[0])
+        assert o["state"] == "done"
+        O, P, L = oracle_trajectory(r[0], r[1], r[2], r[3], 2, 8, 13, 1e-2, 1e-3)
+        assert len(o["loss"]) == len(L)
+        assert np.allclose(o["loss"], L, rtol=1e-4)
+        assert rel_l2(o["O"], O) < 1e-4 and rel_l2(o["P"], P) < 1e-4
+    srv.close()
+
+
 def test_admission_by_budget_and_rejection():
     r = request(**REQS[2])
     big = request(seed=9, S=2, K=1, N=128, H=140, W=140, n_pos=4)
