@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--wave-prec", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage format of the entry-wave copies read by the object gradient")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the single-slice workloads measured beside the headline line")
     ap.add_argument("--dft", default="fft", choices=["fft", "tf32x3", "bf16x3", "tf32"],
                     help="DFT evaluation inside the tile (tensor-core variants: 192x192 window)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps, at most 10)")
@@ -65,6 +67,10 @@ def parse():
     ap.add_argument("--iterations", type=int, default=2, help="iterations per served request")
     ap.add_argument("--max-scan", type=int, default=48, help="largest scan side of a served request")
     ap.add_argument("--rate", type=float, default=16.0, help="mean request arrivals per second")
+    ap.add_argument("--dft-micro", action="store_true",
+                    help="time the DFT evaluations (FFT tile, warp-level tensor-core tiles, tcgen05 row GEMM) on "
+                         "batches of 192 x 192 waves")
+    ap.add_argument("--waves-count", type=int, default=512, help="waves per batch of --dft-micro")
     ap.add_argument("--precision", action="store_true",
                     help="relative L2 error of every DFT mode against the FP64 oracle on a 4-position sub-problem")
     ap.add_argument("--graph", action="store_true",
@@ -198,6 +204,75 @@ def adjoint_algorithmic_flops(wl, items, recompute):
     # conj(O) S, propagator 2(S-1), probe ramp 2
     prods = (2 + S + 2 * (S - 1) + 1 if recompute else 1) + S + S + 2 * (S - 1) + 2
     return items * (ffts * fft_flops(NP) + prods * 6.0 * NP)
+
+
+def hbm_algorithmic_bytes(wl):
+    """Algorithmic HBM bytes of one position's forward + adjoint: the object
+    patch read in the forward and again in the adjoint (S N^2 8 each), the
+    measured pattern (N^2 4) and the object-gradient read-modify-write
+    (S N^2 16); probe and tables stay in L2."""
+    NP = wl.N * wl.N
+    return wl.S * NP * 8 * 2 + NP * 4 + wl.S * NP * 16
+
+
+def workload_leg(wl_id, steps, warmup, dev, fp32_peak_tf, hbm_gbs):
+    """Device-timed steps of another workload of the path (one group per
+    step, Adam included, inputs resident), with its tile kernel's share, its
+    ALU and HBM roofline fractions; reported beside the headline line."""
+    import torch
+    from paper_2505_14372_b300 import AdamState, Context, adam_opt, make_groups, synth
+    wl = synth.WORKLOADS[wl_id]
+    B = wl.B
+    geom = workload_geometry(wl, "recompute")
+    P_np = synth.probe_modes(wl)
+    Pd = torch.from_numpy(P_np).to(dev)
+    Od = torch.ones((wl.S, wl.H, wl.W), dtype=torch.complex64, device=dev)
+    pos_d = torch.from_numpy(synth.raster_positions(wl)).to(dev)
+    Iexp_d = synth.cbed_like_patterns_device(wl, wl.P, device=dev)
+    ng = wl.P // B
+    order = np.concatenate([make_groups(wl.P, B, seed=77, iteration=it, mode="sparse")
+                            for it in range(math.ceil((steps + warmup) / ng) + 1)])
+    idx = torch.from_numpy(order.astype(np.int32)).to(dev)
+    ctx = Context(geom, max_batch=B)
+    st = AdamState(geom, device=dev)
+    opt = adam_opt(lr_O=1e-3, lr_P=1e-4)
+    stats = torch.zeros(2, dtype=torch.float64, device=dev)
+    for i in range(warmup):
+        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, idx[i * B:(i + 1) * B], stats=stats)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(steps):
+        j = warmup + i
+        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, idx[j * B:(j + 1) * B], stats=stats)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # the tile kernel alone, in separate steps with its launches bracketed
+    ctx.set_timing(2)
+    ctx.kernel_times(reset=True)
+    for i in range(steps):
+        j = warmup + i
+        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, idx[j * B:(j + 1) * B], stats=stats)
+    torch.cuda.synchronize()
+    kt = ctx.kernel_times()
+    ctx.set_timing(False)
+    ctx.check_status()
+    ctx.close()
+    tile_ms = kt["adjoint"][0] / kt["adjoint"][1]
+    flops = adjoint_algorithmic_flops(wl, B * wl.K, True)
+    nbytes = hbm_algorithmic_bytes(wl) * B
+    return {"workload": wl.name, "positions_per_s": B / (ms / 1e3), "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "group": B, "loss": {0: "amplitude", 1: "poisson"}[wl.loss],
+            "tile_kernel_ms": tile_ms, "tile_share_of_step": tile_ms / ms,
+            "roofline_alu": {"achieved_tflops": flops / (tile_ms / 1e3) / 1e12, "peak_tflops": fp32_peak_tf,
+                             "frac": flops / (tile_ms / 1e3) / 1e12 / fp32_peak_tf,
+                             "note": "tile kernel's nominal FFT flops over its launch time, of the measured FP32 peak"},
+            "roofline_hbm": {"algorithmic_bytes_per_position": hbm_algorithmic_bytes(wl),
+                             "achieved_gbs_step": nbytes / (ms / 1e3) / 1e9, "peak_gbs": hbm_gbs,
+                             "frac_step": nbytes / (ms / 1e3) / 1e9 / hbm_gbs,
+                             "note": "algorithmic bytes of a whole step over the step time, of the measured copy "
+                                     "bandwidth (the object and patterns of this workload fit in L2)"}}
 
 
 def host_buffer_order(order, used_groups, steps, P, B):
@@ -423,8 +498,63 @@ def run_precision(args):
     return 0
 
 
+def run_dft_micro(args):
+    """The DFT evaluations side by side on batches of N x N waves: the FFT
+    tile and the warp-level tensor-core tiles (2-D transforms, ptycho_fft2_dft)
+    and the tcgen05 row-DFT GEMM (ptycho_dft_rows_tc, one 1-D pass over the
+    rows of every wave).  Times per wave and per 1-D pass (half a 2-D
+    transform), CUDA events, best of the timed repeats; the tcgen05 GEMM's
+    tensor rate against the measured bf16 peak (tf32 at half of it, the
+    nominal ratio)."""
+    import torch
+    from paper_2505_14372_b300.api import dft_rows_tc, dft_rows_tc_check, fft2_dft
+    torch.cuda.set_device(0)
+    N, count = 192, args.waves_count
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    x = torch.complex(torch.randn((count, N, N), generator=g, device="cuda"),
+                      torch.randn((count, N, N), generator=g, device="cuda")).contiguous()
+    peaks, src = measured_peaks()
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    out = {}
+    for dft in ("fft", "tf32x3", "bf16x3", "tf32"):
+        ms = timed(lambda: fft2_dft(x, dft))
+        out[f"tile {dft} (2-D)"] = {"ms": ms, "us_per_wave_2d": 1e3 * ms / count,
+                                    "us_per_wave_pass": 0.5e3 * ms / count}
+    y = torch.empty_like(x)
+    for mode in ("tf32x3", "bf16x3", "tf32"):
+        ms = timed(lambda: dft_rows_tc(x, mode, out=y))
+        prods = 1 if mode == "tf32" else 3
+        flops = 2.0 * count * N * (2 * N) * (2 * N) * prods
+        peak = peaks["bf16_tflops"] * (0.5 if mode.startswith("tf32") else 1.0)
+        out[f"tcgen05 rows {mode} (1-D)"] = {"ms": ms, "us_per_wave_pass": 1e3 * ms / count,
+                                            "tensor_tflops": flops / (ms / 1e3) / 1e12, "peak_tflops": peak,
+                                            "frac": flops / (ms / 1e3) / 1e12 / peak}
+    torch.cuda.synchronize()
+    dft_rows_tc_check()
+    print(json.dumps({"mode": "dft-micro", "config": {"N": N, "waves": count, "peak_source": f"{src} bf16"},
+                      "results": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.dft_micro:
+        return run_dft_micro(args)
     if args.serve:
         return run_serve(args)
     if args.precision:
@@ -644,6 +774,12 @@ def main():
                             "min": float(step_ms.min()), "max": float(step_ms.max()), "n": int(args.steps)},
                 "roofline": roofline, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "last_stats": loss_last}
+        if world == 1 and args.workload == 3 and not (args.positions or args.group) and args.engine == "gd" \
+                and args.dft == "fft" and args.wave_prec == "f32" and args.waves == "recompute" and not args.no_others:
+            # the two single-slice workloads of the path, measured beside the headline
+            line["other_workloads"] = {
+                "1": workload_leg(1, 400, 20, dev, peak_tf, peaks["hbm_gbs"]),
+                "2": workload_leg(2, 200, 10, dev, peak_tf, peaks["hbm_gbs"])}
         if world == 1 and not args.no_baseline:
             n_s = 8 if wl.S > 1 else 64
             line["cpu_baseline"] = cpu_oracle_leg(

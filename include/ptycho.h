@@ -113,6 +113,16 @@ typedef struct {
   int32_t waves;      /* ptycho_waves */
   int32_t dft;        /* ptycho_dft: how the 2-D DFTs are evaluated */
   int32_t wave_prec;  /* ptycho_prec: storage of the entry waves */
+  int32_t deterministic; /* 0: object and probe gradients summed over the
+                            group's positions with float atomics (the
+                            order varies from run to run); 1: each
+                            position's contribution is kept apart and the
+                            sums run in position order, so gradients (and
+                            a step's updates) are bit-identical across
+                            runs; needs the recomputed-wave path with the
+                            FFT tile and FP32 entry waves (EINVAL
+                            otherwise) and B*(S+K)*N*N*8 more bytes of
+                            scratch */
 } ptycho_geom;
 
 typedef struct ptycho_ctx ptycho_ctx;
@@ -332,6 +342,29 @@ int ptycho_exchange_selftest(int32_t N);
  * dir > 0 inverse, both unnormalised).  For tests and diagnostics. */
 int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count,
                 ptycho_stream stream);
+/* ptycho_fft2 through the tile of a given DFT evaluation (ptycho_dft: 0 the
+ * FFT tile, 1-3 the warp-level tensor-core tiles, N = 192 only).  For tests
+ * and for timing the DFT evaluations against each other. */
+int ptycho_fft2_dft(int32_t N, int32_t dft, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count,
+                    ptycho_stream stream);
+
+/* Batched 1-D DFTs of rows on Blackwell's tcgen05 tensor cores (the §2.2
+ * precision option for the DFTs of §3): out[r][n] = sum_k in[r][k]
+ * exp(dir 2 pi i k n / N) for r < rows, N in {64, 128, 192, 256}, dir -1
+ * (forward) or +1 (inverse, unnormalised).  The complex rows are multiplied
+ * by the real 2N x 2N form of the DFT matrix as one GEMM with FP32
+ * accumulation in tensor memory; mode 1 splits both operands into two tf32
+ * parts (three products, near-FP32 accuracy), 2 into two bf16 parts (three
+ * products), 3 takes one tf32 product.  in, out: device arrays
+ * [rows][N] complex64, 16-byte aligned, not overlapping.  The first call
+ * in a CUDA context and (N, mode, dir) builds the split DFT matrix on the
+ * host and uploads it (cudaMalloc + synchronous copy; kept until exit).
+ * EINVAL for bad sizes or pointers or a non-Blackwell device, ECUDA if the
+ * launch fails.  A bounded wait inside the kernel that runs out is reported
+ * by ptycho_dft_rows_tc_check (synchronous) as ETIMEDOUT. */
+int ptycho_dft_rows_tc(int32_t N, int32_t mode, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t rows,
+                       ptycho_stream stream);
+int ptycho_dft_rows_tc_check(void);
 
 /* ---------------------------------------------------------------------------
  * Serving (§2.3 job model, in process): requests from datasets of different

@@ -28,7 +28,7 @@ class Geom(C.Structure):
                 ("H", C.c_int32), ("W", C.c_int32), ("dx", C.c_double), ("lam", C.c_double),
                 ("dz", C.POINTER(C.c_double)), ("bandlimit", C.c_double), ("loss", C.c_int32),
                 ("eps", C.c_double), ("c", C.c_double), ("waves", C.c_int32), ("dft", C.c_int32),
-                ("wave_prec", C.c_int32)]
+                ("wave_prec", C.c_int32), ("deterministic", C.c_int32)]
 
 
 class Opt(C.Structure):
@@ -95,6 +95,9 @@ SIGNATURES = {
     "ptycho_set_step_counter": (I32, [P_, P_]),
     "ptycho_kernel_times": (I32, [P_, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(I32), I32]),
     "ptycho_fft2": (I32, [I32, I32, P_, P_, I32, P_]),
+    "ptycho_fft2_dft": (I32, [I32, I32, I32, P_, P_, I32, P_]),
+    "ptycho_dft_rows_tc": (I32, [I32, I32, I32, P_, P_, I32, P_]),
+    "ptycho_dft_rows_tc_check": (I32, []),
     "ptycho_server_create": (I32, [C.c_size_t, I32, C.POINTER(P_)]),
     "ptycho_server_destroy": (I32, [P_]),
     "ptycho_submit": (I32, [P_, C.POINTER(Request), C.POINTER(C.c_uint64)]),

@@ -53,13 +53,14 @@ class Geometry:
     waves: str = "auto"
     dft: str = "fft"
     wave_prec: str = "f32"
+    deterministic: bool = False
 
     def to_c(self):
         dz = (C.c_double * max(len(self.dz), 1))(*self.dz) if len(self.dz) else None
         g = _lib.Geom(self.S, self.K, self.N, self.N, self.H, self.W, self.dx, self.lam,
                       C.cast(dz, C.POINTER(C.c_double)) if dz is not None else None,
                       self.bandlimit, LOSS[self.loss], self.eps, self.c, WAVES[self.waves], DFT[self.dft],
-                      PREC[self.wave_prec])
+                      PREC[self.wave_prec], 1 if self.deterministic else 0)
         return g, dz
 
 
@@ -358,6 +359,35 @@ def fft2(x: torch.Tensor, inverse=False) -> torch.Tensor:
     out = torch.empty_like(x)
     check(lib().ptycho_fft2(x.shape[-1], 1 if inverse else -1, _ptr(x), _ptr(out), x.shape[0], _stream()))
     return out
+
+
+def fft2_dft(x: torch.Tensor, dft: str = "fft", inverse=False) -> torch.Tensor:
+    """fft2 through the tile of a given DFT evaluation (the tensor-core tiles
+    exist for N = 192)."""
+    assert x.dtype == torch.complex64 and x.is_cuda and x.is_contiguous() and x.dim() == 3
+    out = torch.empty_like(x)
+    check(lib().ptycho_fft2_dft(x.shape[-1], DFT[dft], 1 if inverse else -1, _ptr(x), _ptr(out), x.shape[0],
+                                _stream()))
+    return out
+
+
+TC5 = {"tf32x3": 1, "bf16x3": 2, "tf32": 3}
+
+
+def dft_rows_tc(x: torch.Tensor, mode: str = "tf32x3", inverse=False, out: torch.Tensor | None = None) -> torch.Tensor:
+    """1-D DFT along the last axis of [..., N] complex64 rows on the tcgen05
+    tensor cores (unnormalised; see ptycho_dft_rows_tc)."""
+    assert x.dtype == torch.complex64 and x.is_cuda and x.is_contiguous()
+    N = x.shape[-1]
+    if out is None:
+        out = torch.empty_like(x)
+    check(lib().ptycho_dft_rows_tc(N, TC5[mode], 1 if inverse else -1, _ptr(x), _ptr(out), x.numel() // N,
+                                   _stream()))
+    return out
+
+
+def dft_rows_tc_check():
+    check(lib().ptycho_dft_rows_tc_check())
 
 
 def make_groups(P: int, B: int, seed: int, iteration: int, mode: str = "sparse", pos=None) -> np.ndarray:

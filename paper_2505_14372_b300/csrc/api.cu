@@ -22,9 +22,12 @@ namespace {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// most object blocks of the fused step end (k_step_tail)
+constexpr int kTailMaxBlocks = 4096;
+
 // Offsets of one call's scratch inside the context arena.
 struct Layout {
-  size_t Phat, A, w, gPhat, partials, stats, stage_pos, stage_I, order, omax, wmax, waves, pA, pI, total;
+  size_t Phat, A, w, gPhat, partials, stats, tail, stage_pos, stage_I, order, omax, wmax, waves, pA, pI, det, total;
 };
 
 Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
@@ -45,6 +48,8 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   // and gradient-norm partials
   L.partials = take((size_t)(std::max(ptycho::kLossBlocks, 2 * B) + 3 * ptycho::kNormBlocks + 8) * 8);
   L.stats = take(4 * 8);
+  // fused step end: its block counter, then one FP64 partial per block
+  L.tail = take(256 + (size_t)(g.K + kTailMaxBlocks) * 8);
   L.stage_pos = take((size_t)B * 2 * 4);
   L.stage_I = take((size_t)B * NP * 4);
   L.order = take((size_t)B * 4);  // processing order of a position-major launch
@@ -57,6 +62,9 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   L.waves = take(store ? (size_t)B * g.K * g.S * NP * esize : (size_t)slots * g.K * (g.S + 1) * NP * esize);
   L.pA = take(store ? 0 : (size_t)slots * g.K * NP * 8);
   L.pI = take(store ? 0 : (size_t)slots * NP * 4);
+  // deterministic sums: every position's object patch gradient and probe
+  // spectrum gradient, kept apart
+  L.det = take(g.deterministic ? (size_t)B * (g.S + g.K) * NP * 8 : 0);
   L.total = off;
   return L;
 }
@@ -92,6 +100,10 @@ int ptycho::validate_geom(const ptycho_geom* g) {
   if (g->wave_prec < 0 || g->wave_prec > 2) return perr(PTYCHO_EINVAL, "unknown entry-wave storage format");
   if (g->wave_prec != PTYCHO_PREC_F32 && g->dft != PTYCHO_DFT_FFT)
     return perr(PTYCHO_EINVAL, "16-bit entry waves run with the FFT tile (dft = 0)");
+  if (g->deterministic != 0 && g->deterministic != 1) return perr(PTYCHO_EINVAL, "deterministic must be 0 or 1");
+  if (g->deterministic &&
+      (g->waves == PTYCHO_WAVES_STORE || g->dft != PTYCHO_DFT_FFT || g->wave_prec != PTYCHO_PREC_F32))
+    return perr(PTYCHO_EINVAL, "deterministic sums need recomputed waves, the FFT tile and FP32 entry waves");
   const double cells = (double)g->S * g->H * g->W;
   if (cells > 4.0e9) return perr(PTYCHO_EINVAL, "object too large");
   return PTYCHO_OK;
@@ -141,6 +153,13 @@ struct ptycho_ctx {
   // corrections of the current step
   int64_t* t_dev = nullptr;
   float* bc_dev = nullptr;
+  // fused step end (single-CTA tiles): its grid, 0 when the tile has none.
+  // A gradient step that ended with it leaves g_P^, g_O and the loss
+  // partials cleared; call_seq counts the context's calls, and clean_after
+  // names the call that may skip those memsets (the one right after such a
+  // step, and never one that is being captured).
+  int tail_grid = 0;
+  unsigned long long call_seq = 0, clean_after = ~0ull;
   // timing
   int timing = 0;  // 0 off, 1 every kernel, 2 the tile kernels (forward / adjoint) only
   struct Pending {
@@ -280,6 +299,7 @@ void set_pos_loss(ProblemDesc& d, const float* Iexp, double* lpart, int model, c
 
 int check_call(ptycho_ctx* c, int B) {
   if (!c) return perr(PTYCHO_EINVAL, "context is NULL");
+  ++c->call_seq;
   if (B < 0 || B > c->max_batch)
     return perr(PTYCHO_EINVAL, "B = " + std::to_string(B) + " outside [0, max_batch = " + std::to_string(c->max_batch) + "]");
   int dev = -1;
@@ -295,9 +315,19 @@ int check_call(ptycho_ctx* c, int B) {
 // noise model's derivative (vector-Jacobian product).
 // epie: the seed is the modulus update chi and the per-slice normalisers of
 // §3.3.1 apply (gO, gP then hold the summed ePIE updates).
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// fused_tail: the caller ends the step with k_step_tail, which computes the
+// probe gradient itself (no probe_grad launch here); and if the previous
+// call of this context was such a step (not under capture), g_P^, the
+// context's g_O and the loss partials are already zero.
 int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, const int* idx, int B,
                  int npos, const float* Iexp, ptycho_c64* gO, ptycho_c64* gP, int accumulate, cudaStream_t s, int* nl_out,
-                 bool vjp = false, const float* gI = nullptr, double* gpos = nullptr, bool epie = false) {
+                 bool vjp = false, const float* gI = nullptr, double* gpos = nullptr, bool epie = false,
+                 bool fused_tail = false) {
   const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
   const int K = c->g.K;
   float2* Phat = reinterpret_cast<float2*>(c->arena + L.Phat);
@@ -308,8 +338,9 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
     Timed t(c, "probe_spectrum", s);
     CK(c->ops->probe_spectrum(reinterpret_cast<const float2*>(P), Phat, K, s));
   }
-  CK(cudaMemsetAsync(gPhat, 0, (size_t)K * c->NP * 8, s));
-  if (!accumulate) CK(cudaMemsetAsync(gO, 0, (size_t)nO * 8, s));
+  const bool clean = c->clean_after == c->call_seq && !capturing(s);
+  if (!clean) CK(cudaMemsetAsync(gPhat, 0, (size_t)K * c->NP * 8, s));
+  if (!accumulate && !(clean && reinterpret_cast<float2*>(gO) == c->gO)) CK(cudaMemsetAsync(gO, 0, (size_t)nO * 8, s));
   const int nl = (int)std::min<long long>(ptycho::kLossBlocks, std::max<long long>(1, ((long long)B * c->NP + 255) / 256));
   *nl_out = nl;
   if (B == 0) {
@@ -331,17 +362,24 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
     CK(ptycho::launch_slice_absmax(reinterpret_cast<const float2*>(O), c->g.S, (long long)c->g.H * c->g.W, omax, s));
   }
   // Entry waves recomputed: one position-major loss + adjoint launch (each
-  // cluster takes whole scan positions, all modes in turn).
-  const int variant = epie ? ptycho::kVarEpie : c->g.wave_prec;
+  // cluster takes whole scan positions, all modes in turn).  Deterministic
+  // contexts keep every position's gradients apart and sum them afterwards
+  // in position order.
+  const bool det = c->g.deterministic && !epie && !vjp;
+  const int variant = epie ? ptycho::kVarEpie : det ? ptycho::kVarDet : c->g.wave_prec;
+  if (det) {
+    d.det_gO = reinterpret_cast<float2*>(c->arena + L.det);
+    d.det_gP = d.det_gO + (size_t)c->max_batch * c->g.S * c->NP;
+  }
   if (gpos && !accumulate) CK(cudaMemsetAsync(gpos, 0, (size_t)B * 2 * sizeof(double), s));
   if (!c->store && !vjp && c->pos_clusters > 0) {
     ptycho::PosArgs F = pos_args(c, L);
     int* order = reinterpret_cast<int*>(c->arena + L.order);
     set_pos_loss(d, Iexp, partials, model, c->g);
-    CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
+    if (!clean) CK(cudaMemsetAsync(partials, 0, (size_t)B * 8, s));
     // split: positions [0, B1) first, then the rest once their patterns
     // (copied on another stream) are in; idx-free groups only
-    const int B1 = (c->split_B1 > 0 && c->split_B1 < B && !idx) ? c->split_B1 : B;
+    const int B1 = (c->split_B1 > 0 && c->split_B1 < B && !idx && !det) ? c->split_B1 : B;
     {
       LaunchArgs la = one_position_problem(c, L, d);
       la.d[0].B = B1;
@@ -370,6 +408,12 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
       CK(c->ops->adjoint_pos(la2, F, std::min(B - B1, c->pos_clusters), variant, s));
     }
     *nl_out = B;
+    if (det) {
+      Timed t(c, "det_reduce", s);
+      CK(ptycho::launch_det_reduce(d.det_gO, d.det_gP, pos, idx, npos, B, c->g.S, K, c->g.H, c->g.W, c->N,
+                                   reinterpret_cast<float2*>(gO), gPhat, s));
+    }
+    if (fused_tail) return PTYCHO_OK;
     Timed t(c, "probe_grad", s);
     CK(c->ops->probe_grad(gPhat, reinterpret_cast<float2*>(gP), K, accumulate, s));
     return PTYCHO_OK;
@@ -400,6 +444,7 @@ int run_gradient(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const 
     const int cl = c->store ? std::min(items, c->res_adj) : std::min({items, c->res_rec, c->slots * K});
     CK(c->ops->adjoint(la, cl, c->store, variant, s));
   }
+  if (fused_tail) return PTYCHO_OK;
   {
     Timed t(c, "probe_grad", s);
     CK(c->ops->probe_grad(gPhat, reinterpret_cast<float2*>(gP), K, accumulate, s));
@@ -449,7 +494,7 @@ static int create_impl(const ptycho_geom* geom, int32_t max_batch, size_t scratc
   // waves mode
   const Layout Ls = make_layout(c->g, max_batch, true, 0);
   const Layout Lr = make_layout(c->g, max_batch, false, external_slots ? 0 : c->slots);
-  if (external_slots) c->store = false;
+  if (external_slots || geom->deterministic) c->store = false;
   else if (geom->waves == PTYCHO_WAVES_STORE) c->store = true;
   else if (geom->waves == PTYCHO_WAVES_RECOMPUTE) c->store = false;
   else c->store = scratch_budget_bytes == 0 || Ls.total <= scratch_budget_bytes;
@@ -470,6 +515,8 @@ static int create_impl(const ptycho_geom* geom, int32_t max_batch, size_t scratc
     return bail(perr(PTYCHO_ENOMEM, "cudaMalloc of gradient buffers failed"));
   }
   if (cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) return bail(perr(PTYCHO_ECUDA, "memset"));
+  c->tail_grid = std::min(c->ops->tail_blocks((long long)nO, geom->K), geom->K + kTailMaxBlocks);
+  if (cudaMemset(c->arena + L.tail, 0, 256) != cudaSuccess) return bail(perr(PTYCHO_ECUDA, "memset"));
   // separable Fresnel chirp per gap, in spectral slot order (FP64 phase in turns, reduced)
   if (geom->S > 1) {
     std::vector<float2> h((size_t)(geom->S - 1) * c->N);
@@ -618,9 +665,14 @@ static int step_impl(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
         std::isfinite(opt->lr_O) && std::isfinite(opt->lr_P)))
     return perr(PTYCHO_EINVAL, "bad Adam parameters");
   const Layout L = make_layout(c->g, c->max_batch, c->store, c->slots);
+  const bool tv0 = opt->reg_obj_tv != 0.f || opt->reg_obj_layers_tv != 0.f;
+  const bool reg0 = opt->reg_obj_l2 != 0.f || opt->reg_obj_tikhonov != 0.f || opt->reg_obj_layers != 0.f ||
+                    opt->reg_probe_l2 != 0.f || tv0;
+  // single-CTA tiles without regularisers end the step in one fused launch
+  const bool fused = c->tail_grid > 0 && !reg0;
   int nl = 0;
   int rc = run_gradient(c, O, P, pos_all, idx, B, n_pos, I_exp_all, reinterpret_cast<ptycho_c64*>(c->gO),
-                        reinterpret_cast<ptycho_c64*>(c->gP), 0, s, &nl);
+                        reinterpret_cast<ptycho_c64*>(c->gP), 0, s, &nl, false, nullptr, nullptr, false, fused);
   if (rc) return rc;
   double* partials = reinterpret_cast<double*>(c->arena + L.partials);
   double* stats = stats_out ? stats_out : reinterpret_cast<double*>(c->arena + L.stats);
@@ -641,6 +693,44 @@ static int step_impl(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
   const int64_t t = st->t + 1;
   const float bc1 = (float)(1.0 / (1.0 - std::pow((double)opt->beta1, (double)t)));
   const float bc2 = (float)(1.0 / (1.0 - std::pow((double)opt->beta2, (double)t)));
+  if (fused) {
+    Timed tm(c, "step_tail", s);
+    const float* bcd = nullptr;
+    if (c->t_dev) {
+      CK(ptycho::launch_adam_count(reinterpret_cast<long long*>(c->t_dev), opt->beta1, opt->beta2, c->bc_dev, s));
+      bcd = c->bc_dev;
+    }
+    ptycho::TailArgs A{};
+    A.gPhat = reinterpret_cast<float2*>(c->arena + L.gPhat);
+    A.P = reinterpret_cast<float2*>(P);
+    A.mP = reinterpret_cast<float2*>(st->mP);
+    A.vP = st->vP;
+    A.O = reinterpret_cast<float2*>(O);
+    A.mO = reinterpret_cast<float2*>(st->mO);
+    A.vO = st->vO;
+    A.gO = c->gO;
+    A.nO = nO;
+    A.K = c->g.K;
+    A.update_probe = opt->update_probe ? 1 : 0;
+    A.lrO = opt->lr_O;
+    A.lrP = opt->lr_P;
+    A.b1 = opt->beta1;
+    A.b2 = opt->beta2;
+    A.eps = opt->eps;
+    A.bc1 = bc1;
+    A.bc2 = bc2;
+    A.bcd = bcd;
+    A.lossp = partials;
+    A.nl = nl;
+    A.nz = std::max(nl, c->max_batch);
+    A.normp = reinterpret_cast<double*>(c->arena + L.tail + 256);
+    A.stats = stats;
+    A.counter = reinterpret_cast<unsigned*>(c->arena + L.tail);
+    CK(c->ops->step_tail(A, c->tail_grid, s));
+    if (!capturing(s)) c->clean_after = c->call_seq + 1;
+    st->t = t;
+    return PTYCHO_OK;
+  }
   {
     // the Adam launches also write the |g|^2 partials of the gradients they read
     Timed tm(c, "adam", s);
@@ -694,7 +784,7 @@ int ptycho_step_host(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
   // the first round's patterns are copied ahead of the compute; the rest
   // travel on the context's copy stream while that round runs.
   int B1 = B;
-  if (!c->store && c->pos_clusters > 0 && B > c->pos_clusters) {
+  if (!c->store && c->pos_clusters > 0 && B > c->pos_clusters && !c->g.deterministic) {
     if (!c->copy_stream) {
       CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&c->copied, cudaEventDisableTiming));
@@ -940,6 +1030,18 @@ int ptycho_kernel_times(ptycho_ctx* c, const char** names, double* ms, int32_t* 
 int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count, ptycho_stream stream) {
   const EngineOps* ops = ptycho::engine_for(N);
   if (!ops) return perr(PTYCHO_EINVAL, "N not in {64, 128, 192, 256}");
+  if (dir == 0 || count < 0 || (count > 0 && (!in || !out))) return perr(PTYCHO_EINVAL, "bad arguments");
+  if (count == 0) return PTYCHO_OK;
+  CK(ops->fft_debug(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), count, dir,
+                    static_cast<cudaStream_t>(stream)));
+  return PTYCHO_OK;
+}
+
+int ptycho_fft2_dft(int32_t N, int32_t dft, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count,
+                    ptycho_stream stream) {
+  if (dft < 0 || dft > 3) return perr(PTYCHO_EINVAL, "unknown dft mode");
+  const EngineOps* ops = ptycho::engine_for(N, dft);
+  if (!ops) return perr(PTYCHO_EINVAL, "no tile for this N and dft mode");
   if (dir == 0 || count < 0 || (count > 0 && (!in || !out))) return perr(PTYCHO_EINVAL, "bad arguments");
   if (count == 0) return PTYCHO_OK;
   CK(ops->fft_debug(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), count, dir,

@@ -61,18 +61,7 @@ __global__ void __launch_bounds__(kRedThreads) k_adam(float2* __restrict__ z, fl
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const float2 gg = g[e];
     if (partials) acc += (double)gg.x * gg.x + (double)gg.y * gg.y;
-    float2 mm = m[e];
-    mm.x = fmaf(b1, mm.x, (1.0f - b1) * gg.x);
-    mm.y = fmaf(b1, mm.y, (1.0f - b1) * gg.y);
-    const float vv = fmaf(b2, v[e], (1.0f - b2) * cabs2(gg));
-    const float den = sqrtf(vv * bc2) + eps;
-    const float s = lr * bc1 / den;
-    float2 zz = z[e];
-    zz.x -= s * mm.x;
-    zz.y -= s * mm.y;
-    z[e] = zz;
-    m[e] = mm;
-    v[e] = vv;
+    adam_elem(z, m, v, e, gg, lr, b1, b2, eps, bc1, bc2);
   }
   if (partials) {
     const double t = block_sum(acc, sh);
@@ -410,6 +399,108 @@ cudaError_t launch_weighted_update(float2* z, const float2* dz, const float* aw,
   k_weighted_update<<<grid_for(n), 256, 0, s>>>(z, dz, aw, w, beta, n, period);
   return cudaGetLastError();
 }
+// ---- deterministic gradient sums (geometry flag `deterministic`) ----------
+// Object: one thread per object pixel of a 32 x 8 tile of one slice.  The
+// group's positions are taken in chunks of kDetChunk in index order; each
+// chunk's positions whose window meets the tile are compacted in that order
+// (warp ballots, then the warps' offsets), and every thread adds the patch
+// values of those that cover its pixel.  The sum therefore runs over the
+// positions in index order whatever the launch's processing order was.
+// Positions whose window leaves the object (skipped by the tile kernel) are
+// skipped here by the same test.
+constexpr int kDetTileX = 32, kDetTileY = 8, kDetChunk = 256;
+__global__ void __launch_bounds__(kDetChunk) k_det_object_reduce(const float2* __restrict__ patches,
+                                                                  const float* __restrict__ pos,
+                                                                  const int* __restrict__ idx, int npos, int B, int S,
+                                                                  int H, int W, int N, float2* __restrict__ gO) {
+  __shared__ int list_j[kDetChunk];
+  __shared__ int list_y[kDetChunk];
+  __shared__ int list_x[kDetChunk];
+  __shared__ int warp_n[kDetChunk / 32];
+  __shared__ int total;
+  const int tx = (W + kDetTileX - 1) / kDetTileX, ty = (H + kDetTileY - 1) / kDetTileY;
+  const int s = blockIdx.x / (tx * ty);
+  const int t = blockIdx.x % (tx * ty);
+  const int y0 = (t / tx) * kDetTileY, x0 = (t % tx) * kDetTileX;
+  const int y = y0 + threadIdx.x / kDetTileX, x = x0 + threadIdx.x % kDetTileX;
+  const bool mine = y < H && x < W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t NP = (size_t)N * N;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int c0 = 0; c0 < B; c0 += kDetChunk) {
+    const int j = c0 + (int)threadIdx.x;
+    bool hit = false;
+    int ny = 0, nx = 0;
+    if (j < B) {
+      const int jj = idx ? idx[j] : j;
+      if (jj >= 0 && jj < npos) {
+        const double fy = floor((double)pos[2 * (size_t)jj] + 0.5), fx = floor((double)pos[2 * (size_t)jj + 1] + 0.5);
+        const bool ok = fy >= 0.0 && fx >= 0.0 && fy + N <= (double)H && fx + N <= (double)W;
+        ny = (int)fy;
+        nx = (int)fx;
+        hit = ok && ny < y0 + kDetTileY && ny + N > y0 && nx < x0 + kDetTileX && nx + N > x0;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) warp_n[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int a = 0;
+      for (int w = 0; w < kDetChunk / 32; ++w) {
+        const int n = warp_n[w];
+        warp_n[w] = a;
+        a += n;
+      }
+      total = a;
+    }
+    __syncthreads();
+    if (hit) {
+      const int o = warp_n[warp] + __popc(m & ((1u << lane) - 1u));
+      list_j[o] = j;
+      list_y[o] = ny;
+      list_x[o] = nx;
+    }
+    __syncthreads();
+    if (mine) {
+      for (int i = 0; i < total; ++i) {
+        const int dy = y - list_y[i], dx = x - list_x[i];
+        if (dy >= 0 && dy < N && dx >= 0 && dx < N)
+          acc = cadd(acc, patches[((size_t)list_j[i] * S + s) * NP + (size_t)dy * N + dx]);
+      }
+    }
+    __syncthreads();
+  }
+  if (mine) {
+    float2* g = gO + ((size_t)s * H + y) * W + x;
+    *g = cadd(*g, acc);
+  }
+}
+
+// Probe spectra: gPhat[k][p] += sum over positions j in index order of
+// pgrad[j][k][p].
+__global__ void __launch_bounds__(256) k_det_probe_reduce(const float2* __restrict__ pgrad, int B, long long KNP,
+                                                          float2* __restrict__ gPhat) {
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < KNP; e += (long long)gridDim.x * 256) {
+    float2 a = make_float2(0.f, 0.f);
+    for (int j = 0; j < B; ++j) a = cadd(a, pgrad[(size_t)j * KNP + e]);
+    gPhat[e] = cadd(gPhat[e], a);
+  }
+}
+
+cudaError_t launch_det_reduce(const float2* patches, const float2* pgrad, const float* pos, const int* idx, int npos,
+                              int B, int S, int K, int H, int W, int N, float2* gO, float2* gPhat, cudaStream_t s) {
+  const long long tiles = (long long)((W + kDetTileX - 1) / kDetTileX) * ((H + kDetTileY - 1) / kDetTileY) * S;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  count_launch();
+  k_det_object_reduce<<<(unsigned)tiles, kDetChunk, 0, s>>>(patches, pos, idx, npos, B, S, H, W, N, gO);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long KNP = (long long)K * N * N;
+  count_launch();
+  k_det_probe_reduce<<<(unsigned)std::min<long long>((KNP + 255) / 256, 148LL * 8), 256, 0, s>>>(pgrad, B, KNP, gPhat);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add(float* y, const float* x, long long n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   count_launch();

@@ -25,6 +25,30 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// Complex Adam on element e: m <- b1 m + (1-b1) g; v <- b2 v + (1-b2)|g|^2;
+// z <- z - lr (m bc1) / (sqrt(v bc2) + eps), bc = 1/(1 - beta^t) (§3.2).
+// The update on values held in registers (z, m, v in and out).
+__device__ __forceinline__ void adam_math(float2& z, float2& m, float& v, float2 g, float lr, float b1, float b2,
+                                          float eps, float bc1, float bc2) {
+  m.x = fmaf(b1, m.x, (1.0f - b1) * g.x);
+  m.y = fmaf(b1, m.y, (1.0f - b1) * g.y);
+  v = fmaf(b2, v, (1.0f - b2) * cabs2(g));
+  const float den = sqrtf(v * bc2) + eps;
+  const float s = lr * bc1 / den;
+  z.x -= s * m.x;
+  z.y -= s * m.y;
+}
+__device__ __forceinline__ void adam_elem(float2* __restrict__ z, float2* __restrict__ m, float* __restrict__ v,
+                                          long long e, float2 g, float lr, float b1, float b2, float eps, float bc1,
+                                          float bc2) {
+  float2 zz = z[e], mm = m[e];
+  float vv = v[e];
+  adam_math(zz, mm, vv, g, lr, b1, b2, eps, bc1, bc2);
+  z[e] = zz;
+  m[e] = mm;
+  v[e] = vv;
+}
+
 // I[j][u][v] = sum_k |A[j][k][perm(u)][perm(v)]|^2 / NP (natural order out).
 template <class TL>
 __global__ void k_modesum(const float2* __restrict__ A, float* __restrict__ I, int B, int K) {

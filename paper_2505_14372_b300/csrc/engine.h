@@ -31,6 +31,11 @@ struct EngineOps {
   // launches the bounded-wait self-test (one cluster whose waits run out)
   cudaError_t (*exchange_probe)(cudaStream_t s);
   bool has_variants;  // reduced-precision waves and ePIE are instantiated
+  // fused end of a gradient step (single-CTA tiles; cudaErrorNotSupported
+  // otherwise) and its grid for an object of nO elements and K modes (0:
+  // not available for this tile)
+  cudaError_t (*step_tail)(const TailArgs& A, int blocks, cudaStream_t s);
+  int (*tail_blocks)(long long nO, int K);
 };
 
 const EngineOps* engine_64();
@@ -77,6 +82,11 @@ cudaError_t launch_divide(const float2* num, const float* den, const float* den_
 cudaError_t launch_weighted_update(float2* z, const float2* dz, const float* aw, const float* w, float beta, long long n,
                                    long long period, cudaStream_t s);
 cudaError_t launch_add(float* y, const float* x, long long n, cudaStream_t s);
+// fixed-order sums of the per-position gradients of the deterministic
+// variant: gO [S][H][W] += object patches [B][S][N][N] of the group's
+// positions pos[idx[j]] (index order), gPhat [K][N][N] += pgrad [B][K][N][N]
+cudaError_t launch_det_reduce(const float2* patches, const float2* pgrad, const float* pos, const int* idx, int npos,
+                              int B, int S, int K, int H, int W, int N, float2* gO, float2* gPhat, cudaStream_t s);
 
 // process-wide count of kernels this library has launched (engine_impl /
 // elementwise launchers bump it once per launch)

@@ -28,6 +28,9 @@ struct Engine {
         case kVarLsqStep:
           if constexpr (MAXV >= kVarLsqStep) return f(std::integral_constant<int, kVarLsqStep>{});
           else return cudaErrorNotSupported;
+        case kVarDet:
+          if constexpr (MAXV >= kVarDet) return f(std::integral_constant<int, kVarDet>{});
+          else return cudaErrorNotSupported;
         default: return cudaErrorNotSupported;
       }
     } else {
@@ -135,12 +138,12 @@ struct Engine {
     return cudaGetLastError();
   }
   static cudaError_t adjoint_pos(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s) {
-    return with_variant<kVarLsqStep>(
+    return with_variant<kVarDet>(
         variant, [&](auto v) { return launch(k_adjoint_pos<TL, decltype(v)::value>, clusters, s, L, F); });
   }
   static int resident_pos(int variant) {
     int n = 0;
-    with_variant<kVarLsqStep>(variant, [&](auto v) {
+    with_variant<kVarDet>(variant, [&](auto v) {
       n = resident(k_adjoint_pos<TL, decltype(v)::value>);
       return cudaSuccess;
     });
@@ -173,11 +176,31 @@ struct Engine {
     return v;
   }
 
+  static cudaError_t step_tail(const TailArgs& A, int blocks, cudaStream_t s) {
+    if constexpr (TL::G == 1) return launch(k_step_tail<TL>, blocks, s, A);
+    else return cudaErrorNotSupported;
+  }
+  // K mode blocks plus enough object blocks for one element per thread, at
+  // most one resident wave of them.  Each mode's probe update runs in one
+  // block, so the fused end pays only while a thread's share of a mode is
+  // small: measured, the 64 x 64 step goes 71.6 -> 60.6 us with it (16
+  // elements per thread), the 128 x 128 step 413 -> 419 us (32), so larger
+  // tiles keep the separate launches (0: not used).
+  static int tail_blocks(long long nO, int K) {
+    if constexpr (TL::G == 1 && TL::NP / TL::T <= 16) {
+      const long long need = std::max(1LL, (nO + TL::T - 1) / TL::T);
+      return K + (int)std::min<long long>(need, std::max(1, resident(k_step_tail<TL>)));
+    } else {
+      return 0;
+    }
+  }
+
   static const EngineOps* ops() {
     static const EngineOps o = {TL::N,         TL::G,      TL::T,       TL::R1,      TL::R2,
                                 TL::SMEM,      &probe_spectrum, &forward, &adjoint,  &probe_grad,
                                 &fft_debug,    &modesum,   &loss,       &seed,       &resident_clusters,
-                                &adjoint_pos,  &resident_pos, &take_exchange_timeouts, &exchange_probe, ALLV};
+                                &adjoint_pos,  &resident_pos, &take_exchange_timeouts, &exchange_probe, ALLV,
+                                &step_tail,    &tail_blocks};
     return &o;
   }
 };

@@ -13,6 +13,7 @@
 
 #include <type_traits>
 
+#include "elementwise.cuh"
 #include "launch.h"
 #include "noise.cuh"
 #include "tile.cuh"
@@ -65,6 +66,7 @@ struct Var {
   static constexpr bool epie = V == kVarEpie;         // ePIE normalisers (§3.3.1)
   static constexpr bool lsq_dir = V == kVarLsqDir;    // LSQML direction pass (§3.3.2)
   static constexpr bool lsq_step = V == kVarLsqStep;  // LSQML step-size pass
+  static constexpr bool det = V == kVarDet;           // per-position gradients, fixed-order sums later
   static constexpr size_t wave_bytes = prec ? 4 : 8;
   // entry waves per mode in a slot: S, plus the shifted probe direction in
   // the step pass
@@ -316,6 +318,18 @@ __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
                                              red_add(gOs + (size_t)r * W + c, cscale(cconjmul(p.psi, v), inv_p));
                                              v = cscale(cconjmul(p.o, v), inv_o);
                                            });
+    } else if constexpr (Var<V>::det) {
+      // this position's patch gradient, summed over the modes in mode order
+      // (every element is owned by one thread in every mode: program order)
+      float2* pg = D.det_gO + ((size_t)g.j * D.S + s) * TL::NP;
+      const bool first = g.k == 0;
+      TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, PrePsiO<0>{wv, N, Os, W},
+                                           [&](int r, int c, float2& v, const PsiO& p) {
+                                             const float2 t = cconjmul(p.psi, v);
+                                             float2* q = pg + r * N + c;
+                                             *q = first ? t : cadd(*q, t);
+                                             v = cconjmul(p.o, v);
+                                           });
     } else {
       TL::template row_strided<true, true>(sm.wave, sm.twS, rank, NoLoad{}, PrePsiO<Var<V>::prec>{wv, N, Os, W},
                                            [&](int r, int c, float2& v, const PsiO& p) {
@@ -336,6 +350,7 @@ __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
       // piecewise constant): dL/d(delta_y) = 2 pi / (N NP) sum f_u Im(w),
       // w = conj(F g_psi_0) ramp F P, likewise for x with f_v.
       float2* gP = D.gPhat + (size_t)g.k * TL::NP;
+      float2* gPj = Var<V>::det ? D.det_gP + ((size_t)g.j * D.K + g.k) * TL::NP : nullptr;
       const float2* Ph = D.Phat + (size_t)g.k * TL::NP;
       const float2* rY = sm.rampY;
       const float2* rX = sm.rampX;
@@ -343,7 +358,8 @@ __device__ void adjoint_chain(const Smem<TL>& sm, int rank, const ProblemDesc& D
       float sy = 0.f, sx = 0.f;
       TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
         const float2 ramp = cmul(rY[pu], rX[pv]);
-        red_add(gP + pu * N + pv, cmulc(v, ramp));
+        if constexpr (Var<V>::det) gPj[pu * N + pv] = cmulc(v, ramp);
+        else red_add(gP + pu * N + pv, cmulc(v, ramp));
         if (want_pos) {
           const float w = cconjmul(v, cmul(ramp, __ldg(Ph + pu * N + pv))).y;
           sy = fmaf((float)TL::freq(TL::nat(pu)), w, sy);
@@ -640,6 +656,132 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_grad(const float2* __
   }
   // no CTA leaves while its partner may still be sending to it
   TL::sync_cluster();
+}
+
+// Fused end of a gradient step (TailArgs), single-CTA tiles only.  Blocks
+// [0, K): the probe gradient of mode k through the tile (inverse FFT of
+// g_P^_k / NP), then Adam on P_k straight from the real-space stage; blocks
+// [K, gridDim.x): Adam on the object, grid-stride.  Every block writes the
+// FP64 |g|^2 of the elements it read to normp[block]; the last block to
+// finish sums the loss partials and the norm partials in a fixed order
+// (deterministic for a fixed grid).  Same arithmetic as k_probe_grad,
+// k_adam and k_finalize.
+constexpr int kTailBatch = 8;
+template <class TL>
+__global__ void __launch_bounds__(TL::T, TL::MINB) k_step_tail(const __grid_constant__ TailArgs A) {
+  static_assert(TL::G == 1, "single-CTA tiles");
+  extern __shared__ float4 smem_raw[];
+  __shared__ double sh[32];
+  __shared__ unsigned ticket;
+  constexpr int N = TL::N;
+  const float bc1 = A.bcd ? A.bcd[0] : A.bc1;
+  const float bc2 = A.bcd ? A.bcd[1] : A.bc2;
+  double acc = 0.0;
+  if ((int)blockIdx.x < A.K) {
+    Smem<TL> sm(smem_raw);
+    TL::init_tables(sm.twS, sm.twC, sm.fsq);
+    __syncthreads();
+    const int k = blockIdx.x;
+    float2* src = A.gPhat + (size_t)k * TL::NP;
+    TL::template col_contig<false, false, true>(sm.wave, sm.twC, 0, [&](int pu, int pv) { return src[pu * N + pv]; },
+                                                NoOp{});
+    __syncthreads();
+    // g_P^_k is in shared memory now: clear it for the next step's accumulation
+    for (int e = threadIdx.x; e < TL::NP; e += TL::T) src[e] = make_float2(0.f, 0.f);
+    TL::inverse_tail(sm.wave, sm.twS, sm.twC, 0);
+    // last inverse stage in place (each task writes back the natural-order
+    // samples of the slots it read), then the Adam update over the mode in
+    // natural order with every thread, so that its global accesses coalesce
+    TL::template row_strided<true, false>(sm.wave, sm.twS, 0, NoLoad{}, NoPre{},
+                                          [&](int r, int c, float2& v, const NoPre::type&) {
+                                            sm.wave[TL::rslot(0, c / TL::ROWS, r, c % TL::ROWS)] = v;
+                                          });
+    __syncthreads();
+    const float inv = 1.0f / (float)TL::NP;
+    float2* Pk = A.P + (size_t)k * TL::NP;
+    float2* mk = A.mP + (size_t)k * TL::NP;
+    float* vk = A.vP + (size_t)k * TL::NP;
+    // kTailBatch elements per thread in flight: all loads of a batch are
+    // issued before its stores
+    for (int e0 = threadIdx.x; e0 < TL::NP; e0 += kTailBatch * TL::T) {
+      float2 g[kTailBatch], z[kTailBatch], m[kTailBatch];
+      float v[kTailBatch];
+#pragma unroll
+      for (int u = 0; u < kTailBatch; ++u) {
+        const int e = e0 + u * TL::T;
+        if (e < TL::NP) {
+          const int r = e / N, c = e % N;
+          g[u] = cscale(sm.wave[TL::rslot(0, c / TL::ROWS, r, c % TL::ROWS)], inv);
+          if (A.update_probe) {
+            z[u] = Pk[e];
+            m[u] = mk[e];
+            v[u] = vk[e];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kTailBatch; ++u) {
+        const int e = e0 + u * TL::T;
+        if (e < TL::NP) {
+          acc += (double)g[u].x * g[u].x + (double)g[u].y * g[u].y;
+          if (A.update_probe) {
+            adam_math(z[u], m[u], v[u], g[u], A.lrP, A.b1, A.b2, A.eps, bc1, bc2);
+            Pk[e] = z[u];
+            mk[e] = m[u];
+            vk[e] = v[u];
+          }
+        }
+      }
+    }
+  } else {
+    const long long stride = (long long)(gridDim.x - A.K) * TL::T;
+    for (long long e0 = (long long)(blockIdx.x - A.K) * TL::T + threadIdx.x; e0 < A.nO; e0 += kTailBatch * stride) {
+      float2 g[kTailBatch], z[kTailBatch], m[kTailBatch];
+      float v[kTailBatch];
+#pragma unroll
+      for (int u = 0; u < kTailBatch; ++u) {
+        const long long e = e0 + u * stride;
+        if (e < A.nO) {
+          g[u] = A.gO[e];
+          z[u] = A.O[e];
+          m[u] = A.mO[e];
+          v[u] = A.vO[e];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kTailBatch; ++u) {
+        const long long e = e0 + u * stride;
+        if (e < A.nO) {
+          acc += (double)g[u].x * g[u].x + (double)g[u].y * g[u].y;
+          adam_math(z[u], m[u], v[u], g[u], A.lrO, A.b1, A.b2, A.eps, bc1, bc2);
+          A.gO[e] = make_float2(0.f, 0.f);
+          A.O[e] = z[u];
+          A.mO[e] = m[u];
+          A.vO[e] = v[u];
+        }
+      }
+    }
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) A.normp[blockIdx.x] = t;
+  // last block done: the final sums, in a fixed order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(A.counter, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < A.nl; i += TL::T) a += __ldcg(A.lossp + i);
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += TL::T) b += __ldcg(A.normp + i);
+  const double ta = block_sum(a, sh);
+  const double tb = block_sum(b, sh);
+  for (int i = threadIdx.x; i < A.nz; i += TL::T) A.lossp[i] = 0.0;
+  if (threadIdx.x == 0) {
+    A.stats[0] = ta;
+    A.stats[1] = sqrt(tb);
+    *A.counter = 0u;
+  }
 }
 
 // Self-test of the exchange's bounded wait (tests): every CTA of one cluster

@@ -17,7 +17,10 @@ constexpr int kModelEpie = 3;                      // noise-model id of the ePIE
 // group's illumination; kVarLsqStep recomputes the chain and reduces the
 // per-position least-squares step sizes, then scatters the step-weighted
 // illumination.
-enum Variant { kVarF32 = 0, kVarF16 = 1, kVarBF16 = 2, kVarEpie = 3, kVarLsqDir = 4, kVarLsqStep = 5 };
+// kVarDet (position-major kernel only) keeps each position's object- and
+// probe-gradient contributions apart (ProblemDesc::det_gO / det_gP) instead
+// of adding them with atomics, for fixed-order sums afterwards.
+enum Variant { kVarF32 = 0, kVarF16 = 1, kVarBF16 = 2, kVarEpie = 3, kVarLsqDir = 4, kVarLsqStep = 5, kVarDet = 6 };
 
 // One problem (dataset) inside a launch.  All pointers are device pointers.
 struct ProblemDesc {
@@ -58,6 +61,11 @@ struct ProblemDesc {
   double* lsq_numP;
   double* lsq_denP;
   float* lsq_aw;
+  // deterministic reduction (kVarDet): per-position object-gradient patches
+  // [B][S][NP] (natural order, summed over the modes in mode order) and
+  // probe-spectrum gradients [B][K][NP] (slot order)
+  float2* det_gO;
+  float2* det_gP;
 };
 
 struct LaunchArgs {
@@ -88,6 +96,33 @@ struct PosArgs {
   // clusters take order[cid], order[cid + clusters], ...), or null for
   // 0, 1, ...; outputs stay indexed by position
   const int* order;
+};
+
+// Fused end of a gradient step for single-CTA tiles (N <= 128): probe
+// gradient g_P_k = F^-1 g_P^_k (one block per mode), the complex Adam updates
+// of the probe (from the block's shared memory) and of the object, the FP64
+// |g|^2 block partials, and, in the last block to finish, the final loss and
+// gradient-norm sums.  It also clears what the next step accumulates into
+// (g_P^, g_O and the per-position loss partials), so that step needs no
+// memsets.
+struct TailArgs {
+  float2* gPhat;        // [K][NP] probe spectrum gradient, slot order (read, then zeroed)
+  float2* P;            // [K][NP] probe (updated when update_probe)
+  float2* mP;
+  float* vP;
+  float2* O;            // [nO] object (updated)
+  float2* mO;
+  float* vO;
+  float2* gO;           // [nO] object gradient (read, then zeroed)
+  long long nO;
+  int K, update_probe;
+  float lrO, lrP, b1, b2, eps, bc1, bc2;
+  const float* bcd;     // bias corrections in device memory (step counter on the device), or null
+  double* lossp;        // [nl] loss partials (summed, then [0, nz) zeroed)
+  int nl, nz;
+  double* normp;        // [gridDim.x] FP64 |g|^2 partial of each block
+  double* stats;        // out: [0] loss, [1] gradient norm
+  unsigned* counter;    // blocks done (0 between launches; reset by the last block)
 };
 
 }  // namespace ptycho

@@ -498,6 +498,7 @@ int ptycho_submit(ptycho_server* s, const ptycho_request* q, uint64_t* ticket) {
   if ((q->opt.reg_obj_tv != 0.f || q->opt.reg_obj_layers_tv != 0.f) && !(q->opt.reg_tv_eps > 0.f))
     return perr(PTYCHO_EINVAL, "TV regularisers need reg_tv_eps > 0");
   if (g.wave_prec != PTYCHO_PREC_F32) return perr(PTYCHO_EINVAL, "served requests keep FP32 entry waves");
+  if (g.deterministic) return perr(PTYCHO_EINVAL, "served requests use the atomic gradient sums (deterministic = 0)");
   {
     // host-side validation of the rest of the geometry through a probe context is
     // not possible without allocating; check the fields the kernels rely on

@@ -127,3 +127,19 @@ def test_static_forward_host_validation():
     assert b"static scratch" in lib.ptycho_last_error()
     assert call(Geometry(S=1, K=1, N=64, H=80, W=80), B=-1) == _lib.EINVAL
     assert call(Geometry(S=1, K=1, N=64, H=80, W=80), B=0) == _lib.OK
+
+
+def test_deterministic_flag_validation():
+    """The deterministic flag needs the recomputed-wave FFT path with FP32
+    entry waves; the checks run on the host."""
+    lib = _lib.lib()
+    h = C.c_void_p()
+    for bad in (dict(waves="store"), dict(wave_prec="bf16"), dict(dft="tf32x3", N=192, H=200, W=200)):
+        args = dict(S=1, K=1, N=64, H=80, W=80, deterministic=True)
+        args.update(bad)
+        g, _dz = Geometry(**args).to_c()
+        assert lib.ptycho_create(C.byref(g), 4, 0, C.byref(h)) == _lib.EINVAL
+        assert b"deterministic" in lib.ptycho_last_error()
+    g, _dz = Geometry(S=1, K=1, N=64, H=80, W=80).to_c()
+    g.deterministic = 2
+    assert lib.ptycho_create(C.byref(g), 4, 0, C.byref(h)) == _lib.EINVAL
