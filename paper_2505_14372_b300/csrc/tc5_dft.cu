@@ -12,7 +12,9 @@
 // products hi*hi + lo*hi + hi*lo accumulate in FP32 in tensor memory
 // (TF32X3, BF16X3); TF32X1 takes the single product hi*hi.
 //
-// One CTA (4 warps) computes a 128-row x NT-column tile of Y'.  The
+// One CTA (8 warps) computes MT 128-row x NT-column tiles of Y' (MT = 2 where
+// two accumulators fit the 512 tensor-memory columns and the stages the
+// shared memory: every F' chunk brought in then serves 256 rows).  The
 // reduction dimension K = 2N runs in chunks of 128 bytes per row (32 tf32 or
 // 64 bf16 elements), double-buffered in shared memory:
 //   * the threads load the X' chunk of their rows, split it and store both
@@ -26,8 +28,10 @@
 //     N = NT, K = 8 tf32 / 16 bf16 per instruction, 4 per chunk and part
 //     product) and commits them to the stage's MMA mbarrier, which also
 //     tells the threads when the stage may be refilled.
-// The accumulator (NT FP32 columns x 128 lanes of tensor memory) is read
-// back with tcgen05.ld, each warp its 32 lanes, and written to Y'.  Every
+// The threads hold the next chunk's X' values in registers while the current
+// chunk's MMAs run.  The accumulators (MT NT FP32 columns x 128 lanes of
+// tensor memory) are read back with tcgen05.ld, each warp the 32 lanes of its
+// quarter and half of the columns, and written to Y'.  Every
 // wait is bounded: a wait that runs out sets a flag that
 // ptycho_dft_rows_tc reports as ETIMEDOUT, the CTA waits (bounded) for its
 // MMAs, frees its tensor memory and returns.
@@ -47,7 +51,7 @@
 
 namespace {
 
-constexpr int kTc5Threads = 128;
+constexpr int kTc5Threads = 256;
 constexpr unsigned kTc5Spin = 1u << 24;
 enum { T5_TF32X3 = 1, T5_BF16X3 = 2, T5_TF32X1 = 3 };
 
@@ -128,23 +132,24 @@ __device__ __forceinline__ void mma5(uint32_t d, uint64_t a, uint64_t b, uint32_
   }
 }
 
-// Y'[rows][2N] = X'[rows][2N] F' for one 128 x NT tile; B holds F' as
+// Y'[rows][2N] = X'[rows][2N] F' for MT 128 x NT tiles; B holds F' as
 // [N tiles][chunks][parts][NT rows x 128 bytes] swizzled images.
-template <int MODE, int NT>
+template <int MODE, int NT, int MT>
 __global__ void __launch_bounds__(kTc5Threads, 1) k_dft_rows_tc5(const float* __restrict__ X, float* __restrict__ Y,
                                                                   const uint8_t* __restrict__ B, int rows, int K2) {
   using M5 = T5<MODE>;
-  constexpr int ABYTES = 128 * 128;                // one part of the A chunk
+  constexpr int ABYTES = MT * 128 * 128;           // one part of the A chunk (MT tiles of 128 rows)
   constexpr int BBYTES = NT * 128;                 // one part of the B chunk
   constexpr int STAGE = M5::PARTS * (ABYTES + BBYTES);
-  constexpr uint32_t TCOLS = NT <= 128 ? 128 : 256;
+  constexpr uint32_t TCOLS = MT * NT <= 128 ? 128 : MT * NT <= 256 ? 256 : 512;
+  static_assert(MT * NT <= 512, "accumulators within the tensor memory");
   extern __shared__ uint8_t smem_raw5[];
   __shared__ uint64_t bars[4];                     // load[0..1], mma[2..3]
   __shared__ uint32_t tmem_slot;
   __shared__ int bad;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw5) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * 128;
+  const int m0 = blockIdx.x * 128 * MT;
   const int nt = blockIdx.y;
   const int chunks = K2 / M5::EK;
   const uint32_t load_bar[2] = {su32(&bars[0]), su32(&bars[1])};
@@ -165,9 +170,22 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_dft_rows_tc5(const float* __
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = M5::idesc(NT);
-  // lanes per row of the global chunk (16 bytes of FP32 each)
+  // lanes per row of the global chunk (16 bytes of FP32 each), rows per
+  // round, rounds per chunk: the values of one chunk a thread holds
   constexpr int LPR = M5::EK * 4 / 16;
-  constexpr int RPR = kTc5Threads / LPR;          // rows per load round
+  constexpr int RPR = kTc5Threads / LPR;
+  constexpr int ROUNDS = 128 * MT / RPR;
+  const int q = tid % LPR;
+  float4 v[ROUNDS];
+  auto load_chunk = [&](int c) {
+#pragma unroll
+    for (int i = 0; i < ROUNDS; ++i) {
+      const int m = m0 + i * RPR + tid / LPR;
+      v[i] = m < rows ? __ldg(reinterpret_cast<const float4*>(X + (size_t)m * K2 + (size_t)c * M5::EK) + q)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  load_chunk(0);
   int committed = 0;
   for (int c = 0; c < chunks; ++c) {
     const int st = c & 1, use = c >> 1;
@@ -187,30 +205,31 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_dft_rows_tc5(const float* __
           "l"(src), "r"((uint32_t)(M5::PARTS * BBYTES)), "r"(load_bar[st])
           : "memory");
     }
-    // A chunk: rows m0..m0+127, K elements c*EK..c*EK+EK-1, split and swizzled
-#pragma unroll 2
-    for (int rr = 0; rr < 128; rr += RPR) {
-      const int r = rr + tid / LPR, q = tid % LPR;
-      const int m = m0 + r;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m < rows) v = __ldg(reinterpret_cast<const float4*>(X + (size_t)m * K2 + (size_t)c * M5::EK) + q);
+    // A chunk: rows m0..m0+128 MT-1, K elements c*EK..c*EK+EK-1 (held in
+    // v), split and swizzled
+#pragma unroll
+    for (int i = 0; i < ROUNDS; ++i) {
+      const int r = i * RPR + tid / LPR;
+      const float4 vv = v[i];
       const int kb = q * 4 * M5::ESZ;              // byte offset of this lane's first element in the row
       const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((((kb >> 4) ^ (r & 7))) << 4) + (kb & 15);
       if constexpr (M5::BF) {
-        const uint32_t h0 = bf16x2(v.x, v.y), h1 = bf16x2(v.z, v.w);
-        const float r0 = v.x - __uint_as_float(h0 << 16), r1 = v.y - __uint_as_float(h0 & 0xffff0000u);
-        const float r2 = v.z - __uint_as_float(h1 << 16), r3 = v.w - __uint_as_float(h1 & 0xffff0000u);
+        const uint32_t h0 = bf16x2(vv.x, vv.y), h1 = bf16x2(vv.z, vv.w);
+        const float r0 = vv.x - __uint_as_float(h0 << 16), r1 = vv.y - __uint_as_float(h0 & 0xffff0000u);
+        const float r2 = vv.z - __uint_as_float(h1 << 16), r3 = vv.w - __uint_as_float(h1 & 0xffff0000u);
         *reinterpret_cast<uint2*>(A0 + off) = make_uint2(h0, h1);
         *reinterpret_cast<uint2*>(A0 + ABYTES + off) = make_uint2(bf16x2(r0, r1), bf16x2(r2, r3));
       } else {
-        const uint32_t h0 = to_tf32(v.x), h1 = to_tf32(v.y), h2 = to_tf32(v.z), h3 = to_tf32(v.w);
+        const uint32_t h0 = to_tf32(vv.x), h1 = to_tf32(vv.y), h2 = to_tf32(vv.z), h3 = to_tf32(vv.w);
         *reinterpret_cast<uint4*>(A0 + off) = make_uint4(h0, h1, h2, h3);
         if constexpr (M5::X3)
           *reinterpret_cast<uint4*>(A0 + ABYTES + off) =
-              make_uint4(to_tf32(v.x - __uint_as_float(h0)), to_tf32(v.y - __uint_as_float(h1)),
-                         to_tf32(v.z - __uint_as_float(h2)), to_tf32(v.w - __uint_as_float(h3)));
+              make_uint4(to_tf32(vv.x - __uint_as_float(h0)), to_tf32(vv.y - __uint_as_float(h1)),
+                         to_tf32(vv.z - __uint_as_float(h2)), to_tf32(vv.w - __uint_as_float(h3)));
       }
     }
+    // the next chunk's values travel while this chunk is multiplied
+    if (c + 1 < chunks) load_chunk(c + 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -221,12 +240,17 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_dft_rows_tc5(const float* __
         const uint32_t a_hi = su32(A0), a_lo = su32(A0 + ABYTES);
         const uint32_t b_hi = su32(B0), b_lo = su32(B0 + BBYTES);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint32_t o = 32u * ks;
-          mma5<MODE>(tmem, sdesc(a_hi + o), sdesc(b_hi + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
-          if constexpr (M5::X3) {
-            mma5<MODE>(tmem, sdesc(a_lo + o), sdesc(b_hi + o), idesc, 1u);
-            mma5<MODE>(tmem, sdesc(a_hi + o), sdesc(b_lo + o), idesc, 1u);
+        for (int mt = 0; mt < MT; ++mt) {
+          const uint32_t d = tmem + (uint32_t)(mt * NT);      // accumulator columns of tile mt
+          const uint32_t am = (uint32_t)(mt * 128 * 128);    // its 16 atoms of A
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = 32u * ks;
+            mma5<MODE>(d, sdesc(a_hi + am + o), sdesc(b_hi + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            if constexpr (M5::X3) {
+              mma5<MODE>(d, sdesc(a_lo + am + o), sdesc(b_hi + o), idesc, 1u);
+              mma5<MODE>(d, sdesc(a_hi + am + o), sdesc(b_lo + o), idesc, 1u);
+            }
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mma_bar[st])
@@ -252,11 +276,16 @@ __global__ void __launch_bounds__(kTc5Threads, 1) k_dft_rows_tc5(const float* __
   if (!done && tid == 0) atomicOr(&g_tc5_timeouts, 1u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (done) {
-    const int m = m0 + warp * 32 + lane;
+    // warps w and w + 4 share the lanes of quarter w % 4: each takes half of
+    // the accumulator columns
+    const int quarter = warp & 3, half = warp >> 2;
+    constexpr int CPH = MT * NT / 2;
 #pragma unroll 1
-    for (int col = 0; col < NT; col += 32) {
+    for (int cc = half * CPH; cc < (half + 1) * CPH; cc += 32) {
+      const int mt = cc / NT, col = cc % NT;
+      const int m = m0 + mt * 128 + quarter * 32 + lane;
       uint32_t v[32];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cc;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
           "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -356,14 +385,20 @@ struct TableKey {
 std::mutex g_t5_mu;
 std::map<TableKey, uint8_t*> g_t5_tables;
 
+// two 128-row tiles per CTA where the accumulators (2 NT columns) and two
+// stages (2 parts x (2 x 16 KB of A + NT x 128 B of B) each) fit
+template <int NT>
+constexpr int mt_for() { return NT <= 192 ? 2 : 1; }
+
 template <int MODE, int NT>
 cudaError_t launch5(const float* X, float* Y, const uint8_t* B, int rows, int K2, cudaStream_t s) {
   using M5 = T5<MODE>;
-  const size_t smem = 1024 + 2 * (size_t)M5::PARTS * (128 * 128 + NT * 128);
-  auto k = k_dft_rows_tc5<MODE, NT>;
+  constexpr int MT = mt_for<NT>();
+  const size_t smem = 1024 + 2 * (size_t)M5::PARTS * (MT * 128 * 128 + NT * 128);
+  auto k = k_dft_rows_tc5<MODE, NT, MT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((rows + 127) / 128), (unsigned)(K2 / NT));
+  dim3 grid((unsigned)((rows + 128 * MT - 1) / (128 * MT)), (unsigned)(K2 / NT));
   ptycho::count_launch();
   k<<<grid, kTc5Threads, smem, s>>>(X, Y, B, rows, K2);
   return cudaGetLastError();
