@@ -64,8 +64,8 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: seeded Poisson arrivals of mixed-shape requests through ptycho_submit")
     ap.add_argument("--requests", type=int, default=64)
-    ap.add_argument("--iterations", type=int, default=2, help="iterations per served request")
-    ap.add_argument("--max-scan", type=int, default=48, help="largest scan side of a served request")
+    ap.add_argument("--iterations", type=int, default=50, help="iterations per served request")
+    ap.add_argument("--max-scan", type=int, default=128, help="largest scan side of a served request")
     ap.add_argument("--rate", type=float, default=16.0, help="mean request arrivals per second")
     ap.add_argument("--dft-micro", action="store_true",
                     help="time the DFT evaluations (FFT tile, warp-level tensor-core tiles, tcgen05 row GEMM) on "
@@ -402,7 +402,7 @@ def run_serve(args):
     # continuous batching: requests arrive on their own schedule
     srv = Server(budget, max_active=args.requests)
     tickets = []
-    t0 = time.perf_counter()
+    t0 = time.perf_counter()  # the server's clock started just before
     for t_arr, wl in reqs:
         dt = t_arr - (time.perf_counter() - t0)
         if dt > 0:
@@ -413,21 +413,39 @@ def run_serve(args):
     wall = time.perf_counter() - t0
     st = srv.stats()
     positions = sum(wl.P * args.iterations for _, wl in reqs)
+
+    def latency(d):
+        d = np.asarray(d)
+        return {"p50_ms": float(np.percentile(d, 50)), "p99_ms": float(np.percentile(d, 99)),
+                "mean_ms": float(d.mean())}
+
+    # scheduled arrival -> finish of every request (the server's clock starts
+    # with t0), queueing included
+    done_ms = [srv.poll(t)["finish_ms"] for t in tickets]
     served = {"positions_per_s_wall": positions / wall, "positions_per_s_device": st["positions_per_s"],
               "p50_iter_ms": st["p50_iter_ms"], "p99_iter_ms": st["p99_iter_ms"], "wall_s": wall,
+              "request_latency": latency([f - 1e3 * ta for f, (ta, _) in zip(done_ms, reqs)]),
               "launches": st["launches"], "failed": st["failed"]}
     srv.close()
-    # the same requests one at a time
+    # the same requests one at a time on the same arrival schedule: each is
+    # submitted once it has arrived and the one before it is done (first
+    # come, first served; only one request's data held at a time)
     srv = Server(budget, max_active=1)
+    done1 = []
     t0 = time.perf_counter()
-    for _, wl in reqs:
+    for t_arr, wl in reqs:
+        dt = t_arr - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
         tk = submit(srv, wl)
         srv.wait(tk, 3600e3)
+        done1.append(1e3 * (time.perf_counter() - t0 - t_arr))
     wall1 = time.perf_counter() - t0
     st1 = srv.stats()
-    srv.close()
     one = {"positions_per_s_wall": positions / wall1, "positions_per_s_device": st1["positions_per_s"],
-           "p50_iter_ms": st1["p50_iter_ms"], "p99_iter_ms": st1["p99_iter_ms"], "wall_s": wall1}
+           "p50_iter_ms": st1["p50_iter_ms"], "p99_iter_ms": st1["p99_iter_ms"], "wall_s": wall1,
+           "request_latency": latency(done1), "failed": st1["failed"]}
+    srv.close()
     shapes = [(wl.P, wl.N, wl.S, wl.K) for _, wl in reqs]
     line = {"metric": METRIC, "mode": "serve", "value": served["positions_per_s_wall"], "unit": "positions/s",
             "p50_iter_ms": served["p50_iter_ms"], "p99_iter_ms": served["p99_iter_ms"], "n_gpus": 1,
@@ -438,8 +456,8 @@ def run_serve(args):
                        "iterations_per_request": args.iterations, "scan_sides": [32, args.max_scan],
                        "windows": [64, 128, 192, 256], "slices": [1, 30], "modes": [1, 8], "group": 128,
                        "hbm_budget_GB": 150, "positions_total": positions,
-                       "scaled_from": "50 iterations and scans up to 128x128 per request (reduced so one run "
-                                      "takes minutes)",
+                       **({} if args.iterations == 50 and args.max_scan == 128 else
+                          {"scaled_from": "50 iterations and scans up to 128x128 per request"}),
                        "shapes": shapes}}
     print(json.dumps(line), flush=True)
     return 0

@@ -428,7 +428,11 @@ typedef struct {
 int ptycho_server_create(size_t hbm_budget_bytes, int32_t max_active, ptycho_server** out);
 int ptycho_server_destroy(ptycho_server* srv); /* cancels unfinished work */
 /* Non-blocking; copies the request's host arrays.  ENOMEM if the request
- * alone exceeds the budget. */
+ * alone exceeds the budget.  Served requests take 1 <= S <= 32 slices (the
+ * per-window-size slot scratch is sized for 32; EINVAL beyond), the FFT
+ * tile, FP32 entry waves and the atomic gradient sums; those with K <= 8
+ * modes ride in the shared position-major launch of their window size,
+ * more modes in a forward + recomputing adjoint launch pair. */
 int ptycho_submit(ptycho_server* srv, const ptycho_request* req, uint64_t* ticket);
 /* Non-blocking; fills st (and res once DONE).  ENOTFOUND for unknown tickets. */
 int ptycho_poll(ptycho_server* srv, uint64_t ticket, ptycho_status* st, ptycho_result* res);
