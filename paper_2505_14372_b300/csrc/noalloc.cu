@@ -15,15 +15,14 @@
 // holds kStaticScratchBytes until the process exits.  All calls on a device
 // share it, so calls whose work overlaps on the GPU (different streams, or
 // different host threads) race on it; callers must order them.
-#include <cuda.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
 
+#include "ctxid.h"
 #include "engine.h"
 #include "errors.h"
 #include "internal.h"
@@ -44,7 +43,7 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 // primary context re-created after cudaDeviceReset, holds its own copy), so
 // the address is resolved with cudaGetSymbolAddress once per context, with
 // that context current, and cached under the context's unique id
-// (cuCtxGetId, never reused within a process).
+// (current_context_id, never reused within a process).
 struct AddrEntry {
   unsigned long long ctx_id;
   void* addr;
@@ -52,25 +51,6 @@ struct AddrEntry {
 AddrEntry g_addr[kAddrCache] = {};
 int g_addr_next = 0;
 std::mutex g_addr_mu;
-PFN_cuCtxGetCurrent_v4000 g_get_current = nullptr;
-PFN_cuCtxGetId_v12000 g_get_id = nullptr;
-
-int driver_entry_points() {
-  if (g_get_current && g_get_id) return PTYCHO_OK;
-  cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = cudaDriverEntryPointSymbolNotFound;
-  void* f1 = nullptr;
-  void* f2 = nullptr;
-  const cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1);
-  const cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
-  if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
-      q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
-    cudaGetLastError();
-    return perr(PTYCHO_ECUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not available");
-  }
-  g_get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
-  g_get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
-  return PTYCHO_OK;
-}
 
 int resolve_symbol(void** out) {
   void* p = nullptr;
@@ -88,19 +68,17 @@ int resolve_symbol(void** out) {
 // the runtime bind its primary context, on the context's first call).
 int scratch_address(void** out) {
   std::lock_guard<std::mutex> lk(g_addr_mu);
-  int rc = driver_entry_points();
+  unsigned long long id = 0;
+  int rc = ptycho::current_context_id(&id);
   if (rc) return rc;
-  CUcontext ctx = nullptr;
-  if (g_get_current(&ctx) != CUDA_SUCCESS) return perr(PTYCHO_ECUDA, "cuCtxGetCurrent failed");
   void* fresh = nullptr;
-  if (!ctx) {
+  if (id == 0) {
     // no context bound yet: the runtime binds the device's primary context
     // while resolving the symbol
     if ((rc = resolve_symbol(&fresh))) return rc;
-    if (g_get_current(&ctx) != CUDA_SUCCESS || !ctx) return perr(PTYCHO_ECUDA, "no current CUDA context");
+    if ((rc = ptycho::current_context_id(&id))) return rc;
+    if (id == 0) return perr(PTYCHO_ECUDA, "no current CUDA context");
   }
-  unsigned long long id = 0;
-  if (g_get_id(ctx, &id) != CUDA_SUCCESS) return perr(PTYCHO_ECUDA, "cuCtxGetId failed");
   for (const AddrEntry& a : g_addr)
     if (a.addr && a.ctx_id == id) {
       *out = a.addr;

@@ -45,6 +45,7 @@
 #include <string>
 #include <vector>
 
+#include "ctxid.h"
 #include "engine.h"
 #include "errors.h"
 #include "ptycho.h"
@@ -436,22 +437,9 @@ extern "C" int ptycho_dft_rows_tc(int32_t N, int32_t mode, int32_t dir, const pt
   // the table lives per CUDA context (the first call in a context builds
   // and uploads it, synchronously)
   unsigned long long ctx_id = 0;
-  {
-    void* f1 = nullptr;
-    void* f2 = nullptr;
-    cudaDriverEntryPointQueryResult q1, q2;
-    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
-        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess || !f1 ||
-        !f2) {
-      cudaGetLastError();
-      return perr(PTYCHO_ECUDA, "driver entry points not available");
-    }
-    using GetCur = int (*)(void**);
-    using GetId = int (*)(void*, unsigned long long*);
-    void* cx = nullptr;
-    if (reinterpret_cast<GetCur>(f1)(&cx) != 0 || !cx || reinterpret_cast<GetId>(f2)(cx, &ctx_id) != 0)
-      return perr(PTYCHO_ECUDA, "no current CUDA context");
-  }
+  int rc = ptycho::current_context_id(&ctx_id);
+  if (rc) return rc;
+  if (ctx_id == 0) return perr(PTYCHO_ECUDA, "no current CUDA context");
   uint8_t* table = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_t5_mu);

@@ -3,9 +3,12 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <vector>
 
+#include "ctxid.h"
 #include "engine_impl.cuh"
+#include "ptycho.h"
 #include "tile_tc.cuh"
 
 namespace ptycho {
@@ -90,22 +93,23 @@ void fill_table(int mode, int R, int dir, uint32_t* out) {
 }
 
 std::mutex g_mu;
-bool g_ready[64] = {};
+std::set<unsigned long long> g_ready;  // contexts whose tables are filled
 
-// Fills the fragment tables on the current device once.
+// Fills the fragment tables once per CUDA context (a __device__ array
+// exists once per context).
 cudaError_t ensure_tables(int R1, int R2) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (dev >= 0 && dev < 64 && g_ready[dev]) return cudaSuccess;
+  unsigned long long id = 0;
+  if (ptycho::current_context_id(&id) != PTYCHO_OK) return cudaErrorUnknown;
+  if (id != 0 && g_ready.count(id)) return cudaSuccess;
   std::vector<uint32_t> h((size_t)3 * 4 * kTcTableWords, 0u);
   const int modes[3] = {TC_TF32X3, TC_BF16X3, TC_TF32X1};
   for (int mi = 0; mi < 3; ++mi)
     for (int m = 0; m < 4; ++m)
       fill_table(modes[mi], m < 2 ? R1 : R2, (m & 1) ? +1 : -1, &h[((size_t)mi * 4 + m) * kTcTableWords]);
-  e = cudaMemcpyToSymbol(g_tc_tables, h.data(), h.size() * 4);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) g_ready[dev] = true;
+  const cudaError_t e = cudaMemcpyToSymbol(g_tc_tables, h.data(), h.size() * 4);
+  // the copy binds the primary context when none was current
+  if (e == cudaSuccess && (id != 0 || ptycho::current_context_id(&id) == PTYCHO_OK) && id != 0) g_ready.insert(id);
   return e;
 }
 
