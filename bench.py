@@ -164,12 +164,14 @@ def config_dict(wl, waves, dft="fft", wave_prec="f32"):
                 wl.P * wl.N * wl.N * 4 / 1e9, wl.S * wl.H * wl.W * 8 / 1e6)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(N):
+    """Hash of the sources the tile kernels of window N are built from (the
+    shared headers and that window's instantiation unit)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_14372_b300", "csrc")
     for name in ("radix.cuh", "tile.cuh", "kernels.cuh", "elementwise.cuh", "noise.cuh", "launch.h",
-                 "engine_impl.cuh", "tile64.cu", "tile128.cu", "tile192.cu", "tile256.cu"):
+                 "engine_impl.cuh", f"tile{N}.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -233,21 +235,31 @@ def workload_leg(wl_id, steps, warmup, dev, fp32_peak_tf, hbm_gbs):
     Od = torch.ones((wl.S, wl.H, wl.W), dtype=torch.complex64, device=dev)
     pos_d = torch.from_numpy(synth.raster_positions(wl)).to(dev)
     Iexp_d = synth.cbed_like_patterns_device(wl, wl.P, device=dev)
-    ng = wl.P // B
     order = np.concatenate([make_groups(wl.P, B, seed=77, iteration=it, mode="sparse")
-                            for it in range(math.ceil((steps + warmup) / ng) + 1)])
+                            for it in range(max(1, 64 * B // wl.P))])
+    ng = len(order) // B
     idx = torch.from_numpy(order.astype(np.int32)).to(dev)
     ctx = Context(geom, max_batch=B)
     st = AdamState(geom, device=dev)
     opt = adam_opt(lr_O=1e-3, lr_P=1e-4)
     stats = torch.zeros(2, dtype=torch.float64, device=dev)
-    for i in range(warmup):
-        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, idx[i * B:(i + 1) * B], stats=stats)
+    # warm-up by time, not by count: after an idle gap of a second or two the
+    # GPU's clocks take a while to return (a 64 x 64 step measured 58 us
+    # warm and 127 us right after a 2 s pause), so steps of tens of us need
+    # a few hundred ms of work before they are timed
+    t_w = time.perf_counter()
+    i = 0
+    while i < warmup or time.perf_counter() - t_w < 0.5:
+        j = i % ng
+        ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, idx[j * B:(j + 1) * B], stats=stats)
+        i += 1
+        if i % 64 == 0:
+            torch.cuda.synchronize()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for i in range(steps):
-        j = warmup + i
+        j = (warmup + i) % ng
         ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, idx[j * B:(j + 1) * B], stats=stats)
     e1.record()
     torch.cuda.synchronize()
@@ -256,7 +268,7 @@ def workload_leg(wl_id, steps, warmup, dev, fp32_peak_tf, hbm_gbs):
     ctx.set_timing(2)
     ctx.kernel_times(reset=True)
     for i in range(steps):
-        j = warmup + i
+        j = (warmup + i) % ng
         ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, idx[j * B:(j + 1) * B], stats=stats)
     torch.cuda.synchronize()
     kt = ctx.kernel_times()
@@ -771,7 +783,7 @@ def main():
             tj = json.load(f)
         key = f"{dom}/{args.workload}/{args.waves}/{args.wave_prec}" + ("" if args.engine == "gd" else "/" + args.engine)
         # counters are only valid for the kernel source they were taken on
-        if key in tj and tj[key].get("kernel_source") == kernel_source_hash():
+        if key in tj and tj[key].get("kernel_source") == kernel_source_hash(wl.N):
             traffic = tj[key]["bytes_per_item"] * B * wl.K
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved / peak_tf, "traffic": traffic,
@@ -810,8 +822,8 @@ def main():
                 and args.dft == "fft" and args.wave_prec == "f32" and args.waves == "recompute" and not args.no_others:
             # the two single-slice workloads of the path, measured beside the headline
             line["other_workloads"] = {
-                "1": workload_leg(1, 400, 20, dev, peak_tf, peaks["hbm_gbs"]),
-                "2": workload_leg(2, 200, 10, dev, peak_tf, peaks["hbm_gbs"])}
+                "1": workload_leg(1, 8000, 20, dev, peak_tf, peaks["hbm_gbs"]),
+                "2": workload_leg(2, 1200, 10, dev, peak_tf, peaks["hbm_gbs"])}
         if world == 1 and not args.no_baseline:
             n_s = 8 if wl.S > 1 else 64
             line["cpu_baseline"] = cpu_oracle_leg(

@@ -181,13 +181,13 @@ struct Engine {
     else return cudaErrorNotSupported;
   }
   // K mode blocks plus enough object blocks for one element per thread, at
-  // most one resident wave of them.  Each mode's probe update runs in one
-  // block, so the fused end pays only while a thread's share of a mode is
-  // small: measured, the 64 x 64 step goes 71.6 -> 60.6 us with it (16
-  // elements per thread), the 128 x 128 step 413 -> 419 us (32), so larger
-  // tiles keep the separate launches (0: not used).
+  // most one resident wave of them.  Each mode's probe update (and its
+  // inverse FFT) runs in one block, so the fused end pays only for small
+  // windows: measured, the 64 x 64 step goes 71.6 -> 60.6 us with it, the
+  // 128 x 128 step 413 -> 419 us (512 threads) and 411 -> 431 us (1024), so
+  // larger tiles keep the separate launches (0: not used).
   static int tail_blocks(long long nO, int K) {
-    if constexpr (TL::G == 1 && TL::NP / TL::T <= 16) {
+    if constexpr (TL::G == 1 && TL::NP <= 4096) {
       const long long need = std::max(1LL, (nO + TL::T - 1) / TL::T);
       return K + (int)std::min<long long>(need, std::max(1, resident(k_step_tail<TL>)));
     } else {
