@@ -232,3 +232,39 @@ def test_step_with_fixed_probe_parity(N, S, K, H, W):
     assert np.array_equal(host(Pd), P.astype(np.complex64))
     assert abs(stats[0] - L) < TOL_MS * abs(L) and abs(stats[1] - gn) < TOL_MS * gn
     assert rel_l2(host(Od), O2) < 1e-5
+
+
+def test_fused_step_end_between_other_calls():
+    """The 64 x 64 step ends in one fused launch that also clears the
+    gradient accumulators for the next call (which then skips its memsets).
+    Steps interleaved with adjoint and VJP calls on the same context must
+    each still match the oracle (§3.2)."""
+    geom, og, P, O, pos = problem(97, 1, 2, 64, 96, 92, 10, loss="poisson", eps=0.8)
+    geom.waves = "recompute"
+    I_exp = np.random.default_rng(98).poisson(orc.forward(O, P, pos, og) + 0.5).astype(np.float32)
+    ctx = Context(geom, max_batch=10)
+    Od, Pd = dev(O), dev(P)
+    st = AdamState(geom)
+    opt = adam_opt(lr_O=1e-2, lr_P=1e-3)
+    z = np.zeros
+    rO, rP = O.astype(np.complex128), P.astype(np.complex128)
+    mO, vO, mP, vP = z(O.shape, complex), z(O.shape), z(P.shape, complex), z(P.shape)
+    groups = [np.array(g, np.int32) for g in ([0, 3, 6, 9], [1, 4, 7], [2, 5, 8, 0, 1], [9, 8, 7, 6, 5, 4])]
+    for t, g in enumerate(groups, start=1):
+        stats = host(ctx.step(Od, Pd, st, opt, dev(pos), dev(I_exp), dev(g)))
+        rO, rP, mO, vO, mP, vP, L, gn = orc.step(rO, rP, mO, vO, mP, vP, t, pos, I_exp, g, og, 1e-2, 1e-3)
+        assert abs(stats[0] - L) < TOL_S1 * 10 * abs(L) and abs(stats[1] - gn) < TOL_MS * gn, t
+        assert rel_l2(host(Od), rO) < 1e-5 and rel_l2(host(Pd), rP) < 1e-5, t
+        # a different call right after the step, on the updated state
+        Oc, Pc = host(Od).astype(np.complex128), host(Pd).astype(np.complex128)
+        if t % 2:
+            loss, gO, gP = ctx.adjoint(Od, Pd, dev(pos[:7]), dev(I_exp[:7]))
+            L2, eO, eP = orc.gradient(Oc, Pc, pos[:7], I_exp[:7], og)
+            assert abs(float(loss.item()) - L2) < TOL_S1 * 10 * abs(L2)
+            assert rel_l2(host(gO), eO) < TOL_MS and rel_l2(host(gP), eP) < TOL_MS
+        else:
+            gI = np.random.default_rng(t).standard_normal((5, 64, 64)).astype(np.float32)
+            gO, gP = ctx.vjp(Od, Pd, dev(pos[:5]), dev(gI))
+            eO, eP = orc.vjp(Oc, Pc, pos[:5], gI, og)
+            assert rel_l2(host(gO), eO) < TOL_MS and rel_l2(host(gP), eP) < TOL_MS
+    ctx.check_status()
