@@ -75,6 +75,8 @@ def parse():
                     help="time the DFT evaluations (FFT tile, warp-level tensor-core tiles, tcgen05 row GEMM) on "
                          "batches of 192 x 192 waves")
     ap.add_argument("--waves-count", type=int, default=512, help="waves per batch of --dft-micro")
+    ap.add_argument("--paper-context", action="store_true",
+                    help="seconds per full iteration of the paper-shaped case (80x80 scan, 20 slices, 128^2, 1 mode)")
     ap.add_argument("--precision", action="store_true",
                     help="relative L2 error of every DFT mode against the FP64 oracle on a 4-position sub-problem")
     ap.add_argument("--graph", action="store_true",
@@ -542,6 +544,54 @@ def run_precision(args):
     return 0
 
 
+def run_paper_context(args):
+    """Seconds per full iteration (every scan position once, groups of 512,
+    Adam steps) of the paper-shaped multislice case: 80 x 80 scan, 20 slices,
+    128 x 128 window, one mode.  The paper reports under 3 s per iteration
+    for this scan size, slice count and window on an RTX 3080 (context, not
+    a target: another machine, and its mode count is not stated)."""
+    import torch
+    from paper_2505_14372_b300 import AdamState, Context, adam_opt, make_groups, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = synth.PAPER_CONTEXT
+    B = wl.B
+    geom = workload_geometry(wl, "recompute")
+    Pd = torch.from_numpy(synth.probe_modes(wl)).to(dev)
+    Od = torch.ones((wl.S, wl.H, wl.W), dtype=torch.complex64, device=dev)
+    pos_d = torch.from_numpy(synth.raster_positions(wl)).to(dev)
+    Iexp_d = synth.cbed_like_patterns_device(wl, wl.P, device=dev)
+    ctx = Context(geom, max_batch=B)
+    st = AdamState(geom, device=dev)
+    opt = adam_opt(lr_O=1e-3, lr_P=1e-4)
+    stats = torch.zeros(2, dtype=torch.float64, device=dev)
+
+    def iteration(it):
+        perm = torch.from_numpy(make_groups(wl.P, B, seed=6, iteration=it, mode="sparse").astype(np.int32)).to(dev)
+        for g0 in range(0, wl.P, B):
+            ctx.step(Od, Pd, st, opt, pos_d, Iexp_d, perm[g0:g0 + B], stats=stats)
+
+    for it in range(max(args.warmup, 1)):
+        iteration(it)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(args.steps, 1)
+    e0.record()
+    for it in range(n):
+        iteration(args.warmup + it)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.check_status()
+    s_per_iter = e0.elapsed_time(e1) / 1e3 / n
+    print(json.dumps({"mode": "paper-context", "metric": "seconds per full iteration", "value": s_per_iter,
+                      "unit": "s/iteration", "positions_per_s": wl.P / s_per_iter, "iterations": n,
+                      "config": {"workload": wl.name, "positions": wl.P, "group": B, "slices": wl.S, "modes": wl.K,
+                                 "window": wl.N, "object": [wl.H, wl.W]},
+                      "paper": "under 3 s per iteration, 80x80 scan, 20 slices, 128x128 patterns, JAX on one "
+                               "RTX 3080 (§4.1; mode count not stated)"}), flush=True)
+    return 0
+
+
 def run_dft_micro(args):
     """The DFT evaluations side by side on batches of N x N waves: the FFT
     tile and the warp-level tensor-core tiles (2-D transforms, ptycho_fft2_dft)
@@ -599,6 +649,8 @@ def main():
     args = parse()
     if args.dft_micro:
         return run_dft_micro(args)
+    if args.paper_context:
+        return run_paper_context(args)
     if args.serve:
         return run_serve(args)
     if args.precision:

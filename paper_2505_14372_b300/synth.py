@@ -96,6 +96,16 @@ WORKLOADS = {
 }
 
 
+# The multislice case the paper times its iterations on (80 x 80 scan, 20
+# slices, 128 x 128 patterns; mode count and step not stated there: one mode,
+# the 0.6 A step of workload 3), for quoting seconds per iteration beside the
+# paper's own figure.  Not one of the benchmark workloads above.
+PAPER_CONTEXT = Workload(6, "paper-shaped multislice: 20 slices, 1 mode, 128x128 window, 80x80 scan",
+                         S=20, K=1, N=128, H=640, W=640, scan=(80, 80), step_px=6.0, B=512,
+                         loss=1, eps=0.8, c=0.0, dose=5e4, alpha_mrad=24.0,
+                         defocus_A=50.0, C3_A=1e4, weights=(1.0,), atoms_per_slice=410)
+
+
 def rng_for(cid: int, role: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(1000 * int(cid) + int(role)))
 
