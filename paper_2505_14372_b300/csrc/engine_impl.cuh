@@ -39,8 +39,10 @@ struct Engine {
     }
   }
 
+  // PDL: launch with programmatic stream serialization (the kernel waits
+  // with griddepcontrol.wait before reading what earlier kernels wrote)
   template <class K>
-  static cudaError_t launch(K kernel, int clusters, cudaStream_t s, auto... args) {
+  static cudaError_t launch_ex(K kernel, int clusters, bool pdl, cudaStream_t s, auto... args) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -48,15 +50,28 @@ struct Engine {
     cfg.blockDim = dim3(TL::T, 1, 1);
     cfg.dynamicSmemBytes = TL::SMEM;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = TL::G;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    if (TL::G > 1) {
+      attr[n].id = cudaLaunchAttributeClusterDimension;
+      attr[n].val.clusterDim.x = TL::G;
+      attr[n].val.clusterDim.y = 1;
+      attr[n].val.clusterDim.z = 1;
+      ++n;
+    }
+    if (pdl) {
+      attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[n].val.programmaticStreamSerializationAllowed = 1;
+      ++n;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = TL::G > 1 ? 1 : 0;
+    cfg.numAttrs = n;
     count_launch();
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+  }
+  template <class K>
+  static cudaError_t launch(K kernel, int clusters, cudaStream_t s, auto... args) {
+    return launch_ex(kernel, clusters, false, s, args...);
   }
 
   template <class K>
@@ -95,7 +110,7 @@ struct Engine {
   }
 
   static cudaError_t probe_spectrum(const float2* P, float2* Phat, int K, cudaStream_t s) {
-    return launch(k_probe_spectrum<TL>, K, s, P, Phat, K);
+    return launch_ex(k_probe_spectrum<TL>, K, true, s, P, Phat, K);
   }
   static cudaError_t forward(const LaunchArgs& L, int clusters, bool store, int variant, cudaStream_t s) {
     // without stored waves the forward writes the far field only (the
@@ -111,7 +126,7 @@ struct Engine {
     });
   }
   static cudaError_t probe_grad(const float2* gPhat, float2* gP, int K, int acc, cudaStream_t s) {
-    return launch(k_probe_grad<TL>, K, s, gPhat, gP, K, acc);
+    return launch_ex(k_probe_grad<TL>, K, true, s, gPhat, gP, K, acc);
   }
   static cudaError_t fft_debug(const float2* in, float2* out, int count, int dir, cudaStream_t s) {
     const int cl = std::min(count, resident(k_fft_debug<TL>));
@@ -139,7 +154,7 @@ struct Engine {
   }
   static cudaError_t adjoint_pos(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s) {
     return with_variant<kVarDet>(
-        variant, [&](auto v) { return launch(k_adjoint_pos<TL, decltype(v)::value>, clusters, s, L, F); });
+        variant, [&](auto v) { return launch_ex(k_adjoint_pos<TL, decltype(v)::value>, clusters, true, s, L, F); });
   }
   static int resident_pos(int variant) {
     int n = 0;
@@ -177,7 +192,7 @@ struct Engine {
   }
 
   static cudaError_t step_tail(const TailArgs& A, int blocks, cudaStream_t s) {
-    if constexpr (TL::G == 1) return launch(k_step_tail<TL>, blocks, s, A);
+    if constexpr (TL::G == 1) return launch_ex(k_step_tail<TL>, blocks, true, s, A);
     else return cudaErrorNotSupported;
   }
   // K mode blocks plus enough object blocks for one element per thread, at

@@ -73,6 +73,16 @@ struct Var {
   static constexpr int extra_waves = lsq_step ? 1 : 0;
 };
 
+// Programmatic dependent launch: kernels launched with programmatic stream
+// serialization may start while the kernel before them in the stream is
+// finishing; each waits (griddepcontrol.wait: the prerequisite grid has
+// completed and its memory is visible) after its own set-up and before it
+// reads anything an earlier kernel wrote, and lets the next kernel start
+// once its main work is issued.  Both are no-ops in a launch without the
+// attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void red_add1(float* p, float v) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
@@ -501,6 +511,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
   char* slot = L.slots + (size_t)cid * L.slot_stride;
   float2* Ab = F.Abuf + (size_t)cid * F.astride;
   float* Ib = F.Ibuf + (size_t)cid * TL::NP;
+  pdl_wait();
 #pragma unroll 1
   for (int it = cid; it < L.total; it += n_clusters<TL>()) {
     const int jg = F.order ? __ldg(F.order + it) : it;
@@ -600,6 +611,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
       }
     }
   }
+  pdl_trigger();
   // no CTA leaves while its partner may still be sending to it
   TL::sync_cluster();
 }
@@ -612,6 +624,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_spectrum(const float2
   const int rank = my_rank<TL>();
   TL::init_tables(sm.twS, sm.twC, sm.fsq);
   __syncthreads();
+  pdl_wait();
   constexpr int N = TL::N;
 #pragma unroll 1
   for (int k = cluster_id<TL>(); k < K; k += n_clusters<TL>()) {
@@ -625,6 +638,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_spectrum(const float2
     TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{},
                                                [&](int pu, int pv, float2& v) { out[pu * N + pv] = v; });
   }
+  pdl_trigger();
   // no CTA leaves while its partner may still be sending to it
   TL::sync_cluster();
 }
@@ -637,6 +651,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_probe_grad(const float2* __
   const int rank = my_rank<TL>();
   TL::init_tables(sm.twS, sm.twC, sm.fsq);
   __syncthreads();
+  pdl_wait();
   constexpr int N = TL::N;
   const float inv = 1.0f / (float)TL::NP;
 #pragma unroll 1
@@ -674,13 +689,14 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_step_tail(const __grid_cons
   __shared__ double sh[32];
   __shared__ unsigned ticket;
   constexpr int N = TL::N;
-  const float bc1 = A.bcd ? A.bcd[0] : A.bc1;
-  const float bc2 = A.bcd ? A.bcd[1] : A.bc2;
   double acc = 0.0;
   if ((int)blockIdx.x < A.K) {
     Smem<TL> sm(smem_raw);
     TL::init_tables(sm.twS, sm.twC, sm.fsq);
     __syncthreads();
+    pdl_wait();
+    const float bc1 = A.bcd ? A.bcd[0] : A.bc1;  // written by an earlier kernel: after the wait
+    const float bc2 = A.bcd ? A.bcd[1] : A.bc2;
     const int k = blockIdx.x;
     float2* src = A.gPhat + (size_t)k * TL::NP;
     TL::template col_contig<false, false, true>(sm.wave, sm.twC, 0, [&](int pu, int pv) { return src[pu * N + pv]; },
@@ -734,6 +750,9 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_step_tail(const __grid_cons
       }
     }
   } else {
+    pdl_wait();
+    const float bc1 = A.bcd ? A.bcd[0] : A.bc1;
+    const float bc2 = A.bcd ? A.bcd[1] : A.bc2;
     const long long stride = (long long)(gridDim.x - A.K) * TL::T;
     for (long long e0 = (long long)(blockIdx.x - A.K) * TL::T + threadIdx.x; e0 < A.nO; e0 += kTailBatch * stride) {
       float2 g[kTailBatch], z[kTailBatch], m[kTailBatch];
@@ -762,6 +781,7 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_step_tail(const __grid_cons
       }
     }
   }
+  pdl_trigger();
   const double t = block_sum(acc, sh);
   if (threadIdx.x == 0) A.normp[blockIdx.x] = t;
   // last block done: the final sums, in a fixed order
