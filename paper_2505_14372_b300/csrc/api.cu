@@ -48,7 +48,8 @@ Layout make_layout(const ptycho_geom& g, int B, bool store, int slots) {
   // and gradient-norm partials
   L.partials = take((size_t)(std::max(ptycho::kLossBlocks, 2 * B) + 3 * ptycho::kNormBlocks + 8) * 8);
   L.stats = take(4 * 8);
-  // fused step end: its block counter, then one FP64 partial per block
+  // fused step end: its block counter and (at byte 128) the work queue of
+  // the position-major launch, then one FP64 partial per block
   L.tail = take(256 + (size_t)(g.K + kTailMaxBlocks) * 8);
   L.stage_pos = take((size_t)B * 2 * 4);
   L.stage_I = take((size_t)B * NP * 4);
@@ -287,6 +288,7 @@ ptycho::PosArgs pos_args(ptycho_ctx* c, const Layout& L) {
   F.Abuf = reinterpret_cast<float2*>(c->arena + L.pA);
   F.Ibuf = reinterpret_cast<float*>(c->arena + L.pI);
   F.astride = (long long)c->g.K * c->NP;
+  F.queue = reinterpret_cast<unsigned*>(c->arena + L.tail + 128);
   return F;
 }
 void set_pos_loss(ProblemDesc& d, const float* Iexp, double* lpart, int model, const ptycho_geom& g) {
@@ -1101,7 +1103,7 @@ int resident_slots(int N) {
 constexpr int kOrderCap = kMaxDesc * 4096;
 size_t pos_scratch_bytes(int N, int kmodes, int smax) {
   const size_t NP = (size_t)N * N, cl = (size_t)resident_slots(N);
-  return cl * ((size_t)kmodes * (smax + 1) * NP * 8 + (size_t)kmodes * NP * 8 + NP * 4) + (size_t)kOrderCap * 4;
+  return cl * ((size_t)kmodes * (smax + 1) * NP * 8 + (size_t)kmodes * NP * 8 + NP * 4) + (size_t)kOrderCap * 4 + 256;
 }
 PosScratch pos_scratch_at(char* base, int N, int kmodes, int smax) {
   PosScratch p;
@@ -1115,6 +1117,7 @@ PosScratch pos_scratch_at(char* base, int N, int kmodes, int smax) {
   p.I = reinterpret_cast<float*>(reinterpret_cast<char*>(p.A) + (size_t)p.clusters * kmodes * NP * 8);
   p.order = reinterpret_cast<int*>(p.I + (size_t)p.clusters * NP);
   p.order_cap = kOrderCap;
+  p.queue = reinterpret_cast<unsigned*>(p.order + kOrderCap);
   return p;
 }
 
@@ -1160,8 +1163,16 @@ int step_batch_pos(const StepJob* jobs, int n, const PosScratch& ps, unsigned* s
   la.slots = ps.slots;
   la.slot_stride = ps.slot_bytes;
   std::vector<Layout> L(n);
+  // the costliest positions (most slices times modes) first in the launch's
+  // order: the clusters claim positions in that order, so the cheap ones
+  // fill in at the end
+  std::vector<int> by_cost(n);
+  for (int i = 0; i < n; ++i) by_cost[i] = i;
+  auto cost = [&](int i) { return (long long)jobs[i].c->g.K * (2LL * jobs[i].c->g.S + 1); };
+  std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return cost(a) > cost(b); });
   int total = 0;
-  for (int i = 0; i < n; ++i) {
+  for (int q = 0; q < n; ++q) {
+    const int i = by_cost[q];
     const StepJob& J = jobs[i];
     ptycho_ctx* c = J.c;
     L[i] = make_layout(c->g, c->max_batch, false, 0);
@@ -1175,10 +1186,11 @@ int step_batch_pos(const StepJob* jobs, int n, const PosScratch& ps, unsigned* s
     d.item0 = total;
     set_pos_loss(d, J.Iexp, partials, c->g.loss, c->g);
     total += J.B;
-    la.d[i] = d;
+    la.d[q] = d;
   }
   la.total = total;
   PosArgs F{};
+  F.queue = ps.queue;
   F.Abuf = ps.A;
   F.Ibuf = ps.I;
   F.astride = (long long)ps.kmodes * jobs[0].c->NP;

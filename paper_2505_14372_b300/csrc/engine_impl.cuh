@@ -153,6 +153,7 @@ struct Engine {
     return cudaGetLastError();
   }
   static cudaError_t adjoint_pos(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s) {
+    if (!F.queue) return cudaErrorInvalidValue;
     return with_variant<kVarDet>(
         variant, [&](auto v) { return launch_ex(k_adjoint_pos<TL, decltype(v)::value>, clusters, true, s, L, F); });
   }

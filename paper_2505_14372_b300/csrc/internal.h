@@ -43,6 +43,7 @@ struct PosScratch {
   float2* A = nullptr;       // [clusters][kmodes NP]
   float* I = nullptr;        // [clusters][NP]
   int* order = nullptr;      // [order_cap] processing order of a launch's positions
+  unsigned* queue = nullptr; // [2] work queue of a launch (zeroed once by the owner)
   int clusters = 0, kmodes = 0, smax = 0, order_cap = 0;
 };
 // Bytes of a PosScratch for window N (clusters = resident_slots(N)).

@@ -487,17 +487,148 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint(const __grid_consta
   TL::sync_cluster();
 }
 
+// Work queue of the position-major launch (PosArgs::queue): rank 0's thread
+// 0 claims the next entry of the processing order for its cluster and stores
+// it in the claim word of every CTA of the cluster (visible to all of them
+// after the next cluster barrier).
+template <class TL>
+__device__ __forceinline__ void claim_next(int* claim, unsigned* queue, int rank) {
+  if (rank == 0 && threadIdx.x == 0) {
+    const int v = (int)atomicAdd(queue, 1u);
+    if constexpr (TL::G > 1) {
+      const uint32_t a = smem_u32(claim);
+#pragma unroll
+      for (int r = 0; r < TL::G; ++r) st_cluster_s32(cluster_map(a, (uint32_t)r), v);
+    } else {
+      *claim = v;
+    }
+  }
+}
+
+// One scan position of the position-major kernel: entry `it` of the
+// launch's processing order, run by the cluster that holds slot, Ab and Ib
+// (see k_adjoint_pos).
+template <class TL, int V>
+__device__ __forceinline__ void adjoint_position(Smem<TL>& sm, const LaunchArgs& L, const PosArgs& F, int rank,
+                                                 int it, char* slot, float2* Ab, float* Ib) {
+  constexpr int N = TL::N;
+  constexpr float inv = 1.0f / (float)TL::NP;
+  const int jg = F.order ? __ldg(F.order + it) : it;
+  // position j of problem D (item0: its first position in the launch)
+  const ProblemDesc& D = find_desc(L, jg);
+  const int j = jg - D.item0;
+  const int K = D.K;
+  // one mode's entry waves (and, in the LSQML step pass, its shifted probe direction)
+  const size_t wstride = (size_t)(D.S + Var<V>::extra_waves) * TL::NP * Var<V>::wave_bytes;
+  ItemGeo g = item_geo<TL>(D, D.item0 + j * K);
+  if (!g.ok) {  // every mode of this position skips it
+    if (threadIdx.x == 0 && rank == 0) atomicOr(L.status, PTYCHO_STATUS_OUT_OF_BOUNDS);
+    // every CTA has read the claim word before the next claim is stored
+    TL::sync_cluster();
+    return;
+  }
+  make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
+  __syncthreads();
+  const float* E = D.Iexp + (size_t)g.jj * TL::NP;
+  float lsum = 0.f;
+#pragma unroll 1
+  for (int k = 0; k < K; ++k) {
+    if (k) TL::sync_cluster();
+    g.k = k;
+    if constexpr (Var<V>::lsq_step) {
+      // S_j dP_k = F^-1[ramp . F dP_k], natural order, after the mode's entry waves
+      float2* out = reinterpret_cast<float2*>(slot + k * wstride + (size_t)D.S * TL::NP * Var<V>::wave_bytes);
+      const float2* dPh = D.lsq_dPhat + (size_t)k * TL::NP;
+      const float2* rY = sm.rampY;
+      const float2* rX = sm.rampX;
+      TL::template col_contig<false, false, true>(
+          sm.wave, sm.twC, rank,
+          [&](int pu, int pv) { return cscale(cmul(cmul(__ldg(dPh + pu * N + pv), rY[pu]), rX[pv]), inv); },
+          NoOp{});
+      __syncthreads();
+      TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+      TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{}, NoPre{},
+                                            [&](int r, int c, float2& v, const NoPre::type&) { out[r * N + c] = v; });
+      TL::sync_cluster();
+    }
+    forward_chain<TL, V, true>(sm, rank, D, g, slot + k * wstride);
+    float2* Ak = Ab + (size_t)k * TL::NP;
+    const bool first = k == 0, last = k + 1 == K;
+    TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
+      const int p = pu * N + pv;
+      Ak[p] = v;
+      float I = cabs2(v) * inv;
+      if (!first) I += Ib[p];
+      if (!last) {
+        Ib[p] = I;
+      } else {
+        float l, dl;
+        noise_model(D.model, D.eps, D.c, I, __ldg(E + TL::nat(pu) * N + TL::nat(pv)), l, dl);
+        lsum += l;
+        Ib[p] = 2.0f * dl * inv;
+      }
+    });
+  }
+  {
+    double sd = lsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(D.lpart + j, sd);
+  }
+#pragma unroll 1
+  for (int k = 0; k < K; ++k) {
+    TL::sync_cluster();
+    g.k = k;
+    const float2* Ak = Ab + (size_t)k * TL::NP;
+    TL::template col_contig<false, false, true>(
+        sm.wave, sm.twC, rank,
+        [&](int pu, int pv) {
+          const int p = pu * N + pv;
+          return cscale(Ak[p], Ib[p]);
+        },
+        NoOp{});
+    __syncthreads();
+    TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
+    adjoint_chain<TL, V>(sm, rank, D, g, slot + k * wstride);
+  }
+  if constexpr (Var<V>::lsq_step) {
+    // every mode has added its sums: step-weighted illumination
+    // alpha_{s,j} sum_k |psi_{s,k}|^2 over this CTA's rows of the window
+    TL::sync_cluster();
+    const int W = D.W;
+#pragma unroll 1
+    for (int s = 0; s < D.S; ++s) {
+      const double num = __ldcg(D.lsq_num + (size_t)j * D.S + s), den = __ldcg(D.lsq_den + (size_t)j * D.S + s);
+      const float a = den + (double)F.gamma > 0.0 ? (float)(num / (den + (double)F.gamma)) : 0.f;
+      float* aws = D.lsq_aw + (size_t)s * D.H * D.W + (size_t)g.ny * D.W + g.nx;
+      for (int e = threadIdx.x; e < TL::ROWS * N; e += TL::T) {
+        const int r = rank * TL::ROWS + e / N, c = e % N;
+        float w = 0.f;
+        for (int k = 0; k < K; ++k)
+          w += cabs2(__ldcg(reinterpret_cast<const float2*>(slot + k * wstride + (size_t)s * TL::NP * 8) + r * N + c));
+        red_add1(aws + (size_t)r * W + c, a * w);
+      }
+    }
+  }
+}
+
 // Loss + adjoint with the entry waves recomputed, one cluster per scan
 // position (position-major, one launch per step, no waits between
 // clusters; the positions of several problems of one window size may share
-// a launch).  For position j the cluster runs the forward pass of every mode
-// k (entry waves to part k of its slot, far field A_k to its scratch, the
-// intensity summed over modes in its scratch), applies the noise model to
-// the mode sum (loss into lpart[j], seed weight 2 l'(I) / NP in place of I),
-// then runs the backward pass of every mode from the seed w A_k.  Every
-// pixel of the scratch is written and read back by the same thread (the
-// column stage's task mapping), so the scratch needs no synchronisation
-// beyond program order.
+// a launch).  Cluster c takes entry c of the processing order first; when
+// the launch has more positions than clusters, the rest go through the
+// launch's work queue: a cluster claims the next entry when it finishes a
+// position, so that clusters finishing early take more (positions of
+// different problems cost different amounts: S slices, K modes).  Claims
+// are made at the end of a position rather than ahead of it: an early claim
+// would take work from clusters that have not started yet.  For position j the
+// cluster runs the forward pass of every mode k (entry waves to part k of
+// its slot, far field A_k to its scratch, the intensity summed over modes in
+// its scratch), applies the noise model to the mode sum (loss into lpart[j],
+// seed weight 2 l'(I) / NP in place of I), then runs the backward pass of
+// every mode from the seed w A_k.  Every pixel of the scratch is written and
+// read back by the same thread (the column stage's task mapping), so the
+// scratch needs no synchronisation beyond program order.
 template <class TL, int V>
 __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_constant__ LaunchArgs L,
                                                                  const __grid_constant__ PosArgs F) {
@@ -505,115 +636,44 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
   Smem<TL> sm(smem_raw);
   const int rank = my_rank<TL>();
   TL::init_tables(sm.twS, sm.twC, sm.fsq);
-  constexpr int N = TL::N;
-  constexpr float inv = 1.0f / (float)TL::NP;
   const int cid = cluster_id<TL>();
   char* slot = L.slots + (size_t)cid * L.slot_stride;
   float2* Ab = F.Abuf + (size_t)cid * F.astride;
   float* Ib = F.Ibuf + (size_t)cid * TL::NP;
+  // claim word: written at the end of a position, read after the next
+  // cluster barrier, written again only after at least one more (every
+  // position's work holds one: the backward pass of each mode starts with
+  // it, and a skipped position takes one)
+  __shared__ int claim;
+  int it = cid;  // entry of the processing order; < 0: read the claim
   pdl_wait();
 #pragma unroll 1
-  for (int it = cid; it < L.total; it += n_clusters<TL>()) {
-    const int jg = F.order ? __ldg(F.order + it) : it;
-    // position j of problem D (item0: its first position in the launch)
-    const ProblemDesc& D = find_desc(L, jg);
-    const int j = jg - D.item0;
-    const int K = D.K;
-    // one mode's entry waves (and, in the LSQML step pass, its shifted probe direction)
-    const size_t wstride = (size_t)(D.S + Var<V>::extra_waves) * TL::NP * Var<V>::wave_bytes;
-    ItemGeo g = item_geo<TL>(D, D.item0 + j * K);
+  for (;;) {
+    // also: the partner CTAs are done with the previous position
     TL::sync_cluster();
-    if (!g.ok) {  // every mode of this position skips it
-      if (threadIdx.x == 0 && rank == 0) atomicOr(L.status, PTYCHO_STATUS_OUT_OF_BOUNDS);
-      continue;
-    }
-    make_ramps<TL>(sm.rampY, sm.rampX, g.dy, g.dx);
-    __syncthreads();
-    const float* E = D.Iexp + (size_t)g.jj * TL::NP;
-    float lsum = 0.f;
-#pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-      if (k) TL::sync_cluster();
-      g.k = k;
-      if constexpr (Var<V>::lsq_step) {
-        // S_j dP_k = F^-1[ramp . F dP_k], natural order, after the mode's entry waves
-        float2* out = reinterpret_cast<float2*>(slot + k * wstride + (size_t)D.S * TL::NP * Var<V>::wave_bytes);
-        const float2* dPh = D.lsq_dPhat + (size_t)k * TL::NP;
-        const float2* rY = sm.rampY;
-        const float2* rX = sm.rampX;
-        TL::template col_contig<false, false, true>(
-            sm.wave, sm.twC, rank,
-            [&](int pu, int pv) { return cscale(cmul(cmul(__ldg(dPh + pu * N + pv), rY[pu]), rX[pv]), inv); },
-            NoOp{});
-        __syncthreads();
-        TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
-        TL::template row_strided<true, false>(sm.wave, sm.twS, rank, NoLoad{}, NoPre{},
-                                              [&](int r, int c, float2& v, const NoPre::type&) { out[r * N + c] = v; });
-        TL::sync_cluster();
-      }
-      forward_chain<TL, V, true>(sm, rank, D, g, slot + k * wstride);
-      float2* Ak = Ab + (size_t)k * TL::NP;
-      const bool first = k == 0, last = k + 1 == K;
-      TL::template col_contig<true, true, false>(sm.wave, sm.twC, rank, NoLoad{}, [&](int pu, int pv, float2& v) {
-        const int p = pu * N + pv;
-        Ak[p] = v;
-        float I = cabs2(v) * inv;
-        if (!first) I += Ib[p];
-        if (!last) {
-          Ib[p] = I;
-        } else {
-          float l, dl;
-          noise_model(D.model, D.eps, D.c, I, __ldg(E + TL::nat(pu) * N + TL::nat(pv)), l, dl);
-          lsum += l;
-          Ib[p] = 2.0f * dl * inv;
-        }
-      });
-    }
-    {
-      double sd = lsum;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
-      if ((threadIdx.x & 31) == 0) atomicAdd(D.lpart + j, sd);
-    }
-#pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-      TL::sync_cluster();
-      g.k = k;
-      const float2* Ak = Ab + (size_t)k * TL::NP;
-      TL::template col_contig<false, false, true>(
-          sm.wave, sm.twC, rank,
-          [&](int pu, int pv) {
-            const int p = pu * N + pv;
-            return cscale(Ak[p], Ib[p]);
-          },
-          NoOp{});
-      __syncthreads();
-      TL::inverse_tail(sm.wave, sm.twS, sm.twC, rank);
-      adjoint_chain<TL, V>(sm, rank, D, g, slot + k * wstride);
-    }
-    if constexpr (Var<V>::lsq_step) {
-      // every mode has added its sums: step-weighted illumination
-      // alpha_{s,j} sum_k |psi_{s,k}|^2 over this CTA's rows of the window
-      TL::sync_cluster();
-      const int W = D.W;
-#pragma unroll 1
-      for (int s = 0; s < D.S; ++s) {
-        const double num = __ldcg(D.lsq_num + (size_t)j * D.S + s), den = __ldcg(D.lsq_den + (size_t)j * D.S + s);
-        const float a = den + (double)F.gamma > 0.0 ? (float)(num / (den + (double)F.gamma)) : 0.f;
-        float* aws = D.lsq_aw + (size_t)s * D.H * D.W + (size_t)g.ny * D.W + g.nx;
-        for (int e = threadIdx.x; e < TL::ROWS * N; e += TL::T) {
-          const int r = rank * TL::ROWS + e / N, c = e % N;
-          float w = 0.f;
-          for (int k = 0; k < K; ++k)
-            w += cabs2(__ldcg(reinterpret_cast<const float2*>(slot + k * wstride + (size_t)s * TL::NP * 8) + r * N + c));
-          red_add1(aws + (size_t)r * W + c, a * w);
-        }
-      }
+    if (it < 0) it = n_clusters<TL>() + claim;
+    if (it >= L.total) break;
+    adjoint_position<TL, V>(sm, L, F, rank, it, slot, Ab, Ib);
+    // claim the next entry (or leave when there is no queue)
+    if (L.total > n_clusters<TL>()) {
+      claim_next<TL>(&claim, F.queue, rank);
+      it = -1;
+    } else {
+      it = L.total;
     }
   }
   pdl_trigger();
   // no CTA leaves while its partner may still be sending to it
   TL::sync_cluster();
+  // every cluster made its last claim before counting itself out, so the
+  // last one out can reset the queue for the next launch
+  if (L.total > n_clusters<TL>() && rank == 0 && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(F.queue + 1, 1u) == (unsigned)n_clusters<TL>() - 1u) {
+      atomicExch(F.queue, 0u);
+      atomicExch(F.queue + 1, 0u);
+    }
+  }
 }
 
 // Probe spectra P^_k = F P_k in spectral slot order (one item per mode).

@@ -92,10 +92,14 @@ struct PosArgs {
   float* Ibuf;         // [clusters][NP] mode-summed intensity, then 2 l'(I) / NP
   long long astride;   // float2 per cluster in Abuf (>= K NP of every problem)
   float gamma;         // LSQML step-size regulariser
-  // processing order [total]: a permutation of the launch's positions (the
-  // clusters take order[cid], order[cid + clusters], ...), or null for
-  // 0, 1, ...; outputs stay indexed by position
+  // processing order [total]: a permutation of the launch's positions,
+  // taken in this order, or null for 0, 1, ...; outputs stay indexed by
+  // position
   const int* order;
+  // work queue of the launch: [0] next entry of the order to claim, [1]
+  // clusters done.  Both zero when a launch starts; the last cluster to
+  // finish sets them back to zero.
+  unsigned* queue;
 };
 
 // Fused end of a gradient step for single-CTA tiles (N <= 128): probe

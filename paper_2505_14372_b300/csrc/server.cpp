@@ -200,6 +200,8 @@ int ptycho_server::admit(Request* r) {
       C.pos_bytes = pb;
       C.ps = ptycho::pos_scratch_at(C.pos_mem, g.h, kPosModes, kMaxSlices);
       slot_bytes += pb;
+      // the launches' work queue starts empty (each launch leaves it so)
+      if (cudaMemsetAsync(C.ps.queue, 0, 2 * sizeof(unsigned), C.stream) != cudaSuccess) return PTYCHO_ECUDA;
     } else {
       cudaGetLastError();
       C.pos_mem = nullptr;
