@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-others", action="store_true",
                     help="skip the single-slice workloads measured beside the headline line")
-    ap.add_argument("--dft", default="fft", choices=["fft", "tf32x3", "bf16x3", "tf32"],
+    ap.add_argument("--dft", default="fft", choices=["fft", "tf32x3", "bf16x3", "tf32", "bf16x6"],
                     help="DFT evaluation inside the tile (tensor-core variants: 192x192 window)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the host-buffer leg (default: --steps, at most 10)")
     ap.add_argument("--serve", action="store_true",
@@ -516,7 +516,7 @@ def run_precision(args):
     rel = lambda a, b: float(np.linalg.norm((np.asarray(a, np.complex128) - b).ravel()) / np.linalg.norm(b.ravel()))
     out = {}
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    for mode in (["fft", "tf32x3", "bf16x3", "tf32"] if wl.N == 192 else ["fft"]):
+    for mode in (["fft", "tf32x3", "bf16x3", "tf32", "bf16x6"] if wl.N == 192 else ["fft"]):
         geom = workload_geometry(small, args.waves, mode)
         ctx = Context(geom, max_batch=4)
         I = ctx.forward(d(O), d(P), d(pos)).cpu().numpy()
@@ -625,7 +625,7 @@ def run_dft_micro(args):
         return best
 
     out = {}
-    for dft in ("fft", "tf32x3", "bf16x3", "tf32"):
+    for dft in ("fft", "tf32x3", "bf16x3", "tf32", "bf16x6"):
         ms = timed(lambda: fft2_dft(x, dft))
         out[f"tile {dft} (2-D)"] = {"ms": ms, "us_per_wave_2d": 1e3 * ms / count,
                                     "us_per_wave_pass": 0.5e3 * ms / count}

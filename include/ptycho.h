@@ -84,9 +84,17 @@ typedef enum { PTYCHO_WAVES_AUTO = 0, PTYCHO_WAVES_STORE = 1, PTYCHO_WAVES_RECOM
 /* Evaluation of the small DFTs inside the shared-memory FFT tile: radix
  * butterflies on the FP32 CUDA cores (the default), or dense DFT-matrix
  * products on the tensor cores with the FP32 operands split into two tf32 or
- * bf16 terms (three products, near-FP32 accuracy) or a single tf32 product.
- * The tensor-core variants exist for the 192 x 192 window. */
-typedef enum { PTYCHO_DFT_FFT = 0, PTYCHO_DFT_TF32X3 = 1, PTYCHO_DFT_BF16X3 = 2, PTYCHO_DFT_TF32 = 3 } ptycho_dft;
+ * bf16 terms (three products: 22 or 16 significand bits), a single tf32
+ * product, or three bf16 terms (BF16X6: all 24 bits of an FP32 value, the
+ * six largest products, FP32-level accuracy).  The tensor-core variants
+ * exist for the 192 x 192 window. */
+typedef enum {
+  PTYCHO_DFT_FFT = 0,
+  PTYCHO_DFT_TF32X3 = 1,
+  PTYCHO_DFT_BF16X3 = 2,
+  PTYCHO_DFT_TF32 = 3,
+  PTYCHO_DFT_BF16X6 = 4
+} ptycho_dft;
 
 /* Storage format of the entry waves kept between the forward pass and the
  * object-gradient term of the adjoint (the stored array or the recompute
@@ -343,7 +351,7 @@ int ptycho_exchange_selftest(int32_t N);
 int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count,
                 ptycho_stream stream);
 /* ptycho_fft2 through the tile of a given DFT evaluation (ptycho_dft: 0 the
- * FFT tile, 1-3 the warp-level tensor-core tiles, N = 192 only).  For tests
+ * FFT tile, 1-4 the warp-level tensor-core tiles, N = 192 only).  For tests
  * and for timing the DFT evaluations against each other. */
 int ptycho_fft2_dft(int32_t N, int32_t dft, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count,
                     ptycho_stream stream);

@@ -17,7 +17,7 @@ from ._lib import check, lib
 
 LOSS = {"amplitude": 0, "anscombe": 0, "poisson": 1, "gaussian": 2}
 WAVES = {"auto": 0, "store": 1, "recompute": 2}
-DFT = {"fft": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3}
+DFT = {"fft": 0, "tf32x3": 1, "bf16x3": 2, "tf32": 3, "bf16x6": 4}
 PREC = {"f32": 0, "f16": 1, "bf16": 2}
 
 

@@ -80,7 +80,7 @@ int ptycho::validate_geom(const ptycho_geom* g) {
   if (g->h != g->w) return perr(PTYCHO_EINVAL, "window must be square (h == w)");
   if (!ptycho::engine_for(g->h))
     return perr(PTYCHO_EINVAL, "window size " + std::to_string(g->h) + " not in {64, 128, 192, 256}");
-  if (g->dft < 0 || g->dft > 3) return perr(PTYCHO_EINVAL, "unknown dft mode");
+  if (g->dft < 0 || g->dft > 4) return perr(PTYCHO_EINVAL, "unknown dft mode");
   if (g->dft != PTYCHO_DFT_FFT && !ptycho::engine_for(g->h, g->dft))
     return perr(PTYCHO_EINVAL, "the tensor-core DFT variants are built for the 192 x 192 window only");
   if (g->H < g->h || g->W < g->w) return perr(PTYCHO_EINVAL, "object smaller than the window");
@@ -1041,7 +1041,7 @@ int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, i
 
 int ptycho_fft2_dft(int32_t N, int32_t dft, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count,
                     ptycho_stream stream) {
-  if (dft < 0 || dft > 3) return perr(PTYCHO_EINVAL, "unknown dft mode");
+  if (dft < 0 || dft > 4) return perr(PTYCHO_EINVAL, "unknown dft mode");
   const EngineOps* ops = ptycho::engine_for(N, dft);
   if (!ops) return perr(PTYCHO_EINVAL, "no tile for this N and dft mode");
   if (dir == 0 || count < 0 || (count > 0 && (!in || !out))) return perr(PTYCHO_EINVAL, "bad arguments");

@@ -7,7 +7,10 @@
 //   task's elements, zero-padded beyond R), M: 32 x 32 = [[Wr, -Wi], [Wi, Wr]]
 //   with W[m][e] = exp(DIR 2 pi i m e / R).
 // Modes: TF32X3 (x = hi + lo in tf32, hi*hi + hi*lo + lo*hi on m16n8k8),
-// BF16X3 (the same with bf16 on m16n8k16), TF32X1 (one tf32 product).
+// BF16X3 (the same with bf16 on m16n8k16), TF32X1 (one tf32 product),
+// BF16X6 (x = x0 + x1 + x2 in bf16, 8 significand bits each, so the three
+// parts hold all 24 bits of an fp32 value; the six products x_i y_j with
+// i + j <= 2, whose dropped terms are below 2^-24 relative).
 // Fragment ownership (PTX m16n8k8 / m16n8k16 layouts), g = lane/4, t = lane%4:
 //   TF32: lane loads elements {t, t+4, t+8, t+12} of task g;
 //   BF16: lane loads elements {2t, 2t+1, 2t+8, 2t+9} of task g;
@@ -15,6 +18,14 @@
 // The matrices' fragments are tables built on the host in FP64 and split
 // there (tc_tables), indexed [lane][register] so that each lane's loads are
 // contiguous.
+// Accumulation in the split modes: the MMA adds its accumulator input to the
+// products after aligning them to the largest and truncating, so every MMA
+// whose input already holds the full-size result loses low bits of it.  The
+// small cross products therefore run as one chain of their own (its sums
+// stay 2^-8 or less of the result), while the leading product of each
+// k-step starts from a zero accumulator and the k-steps' leading sums are
+// added with round-to-nearest fp32 adds: two (bf16) or four (tf32)
+// truncations at full size per output instead of one per MMA.
 #pragma once
 #include <stdint.h>
 
@@ -22,7 +33,14 @@
 
 namespace ptycho {
 
-enum TcMode { TC_NONE = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_TF32X1 = 3 };
+enum TcMode { TC_NONE = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_TF32X1 = 3, TC_BF16X6 = 4 };
+constexpr int kTcModes = 4;
+
+template <int MODE>
+__host__ __device__ constexpr bool tc_is_bf16() { return MODE == TC_BF16X3 || MODE == TC_BF16X6; }
+// operand parts of a split mode
+template <int MODE>
+__host__ __device__ constexpr int tc_parts() { return MODE == TC_BF16X6 ? 3 : MODE == TC_TF32X1 ? 1 : 2; }
 
 // words per lane in a fragment table (the TF32x3 size; BF16x3 uses half)
 constexpr int kTcLaneWords = 64;
@@ -30,8 +48,9 @@ constexpr int kTcLaneWords = 64;
 // registers of A fragments per lane for one (R, DIR) matrix
 template <int MODE>
 struct TcRegs {
-  // TF32: 2 m-tiles x 4 k-steps x 4 regs, hi and lo; BF16: 2 x 2 x 4, hi and lo
-  static constexpr int N = MODE == TC_BF16X3 ? 32 : 64;
+  // TF32: 2 m-tiles x 4 k-steps x 4 regs, hi and lo; BF16: 2 x 2 x 4 per
+  // part (two parts, or three for BF16X6)
+  static constexpr int N = MODE == TC_BF16X6 ? 48 : MODE == TC_BF16X3 ? 32 : 64;
 };
 
 __device__ __forceinline__ uint32_t f2tf32(float x) {
@@ -47,6 +66,18 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
 }
 __device__ __forceinline__ float bf16_lo_as_float(uint32_t p) { return __uint_as_float(p << 16); }
 __device__ __forceinline__ float bf16_hi_as_float(uint32_t p) { return __uint_as_float(p & 0xffff0000u); }
+// (v0, v1) as PARTS packed bf16 pairs, most significant first: each part is
+// the rounded remainder of the ones before it (the remainders are exact in
+// fp32)
+template <int PARTS>
+__device__ __forceinline__ void split_bf16(float v0, float v1, uint32_t (&p)[PARTS]) {
+#pragma unroll
+  for (int i = 0; i < PARTS; ++i) {
+    p[i] = pack_bf16(v0, v1);
+    v0 -= bf16_lo_as_float(p[i]);
+    v1 -= bf16_hi_as_float(p[i]);
+  }
+}
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -80,39 +111,59 @@ template <int MODE, int R, class Ld, class St>
 __device__ __forceinline__ void tc_dft8(const TcMat<MODE>& M, int task0, const Ld& ld, const St& st) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
-  float d[2][4];
+  // d: result (the one chain of TF32X1, else the small cross products);
+  // e: the split modes' leading products, summed one k-step at a time
+  float d[2][4], e[2][4];
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) d[mt][i] = 0.f;
-  if constexpr (MODE == TC_BF16X3) {
+    for (int i = 0; i < 4; ++i) d[mt][i] = e[mt][i] = 0.f;
+  // leading product of one k-step from a zero accumulator, added to e
+  auto lead = [&](int mt, float(&t)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) e[mt][i] += t[i];
+  };
+  if constexpr (tc_is_bf16<MODE>()) {
+    constexpr int NPART = tc_parts<MODE>();
     // elements 2t, 2t+1, 2t+8, 2t+9 of task g
     float2 x[4];
     const int es[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
 #pragma unroll
     for (int j = 0; j < 4; ++j) x[j] = es[j] < R ? ld(task0 + g, es[j]) : make_float2(0.f, 0.f);
-    // k-step 0: real parts, k-step 1: imaginary parts
-    uint32_t bh[2][2], bl[2][2];
+    // k-step 0: real parts, k-step 1: imaginary parts; b[ks][r][part]
+    uint32_t b[2][2][NPART];
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
-      const float v0 = ks ? x[0].y : x[0].x, v1 = ks ? x[1].y : x[1].x;
-      const float v2 = ks ? x[2].y : x[2].x, v3 = ks ? x[3].y : x[3].x;
-      bh[ks][0] = pack_bf16(v0, v1);
-      bh[ks][1] = pack_bf16(v2, v3);
-      bl[ks][0] = pack_bf16(v0 - bf16_lo_as_float(bh[ks][0]), v1 - bf16_hi_as_float(bh[ks][0]));
-      bl[ks][1] = pack_bf16(v2 - bf16_lo_as_float(bh[ks][1]), v3 - bf16_hi_as_float(bh[ks][1]));
+      split_bf16<NPART>(ks ? x[0].y : x[0].x, ks ? x[1].y : x[1].x, b[ks][0]);
+      split_bf16<NPART>(ks ? x[2].y : x[2].x, ks ? x[3].y : x[3].x, b[ks][1]);
     }
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
-        const uint32_t* ah = &M.a[(mt * 2 + ks) * 4];
-        const uint32_t* al = &M.a[16 + (mt * 2 + ks) * 4];
-        const uint32_t AH[4] = {ah[0], ah[1], ah[2], ah[3]};
-        const uint32_t AL[4] = {al[0], al[1], al[2], al[3]};
-        mma_bf16(d[mt], AL, bh[ks][0], bh[ks][1]);
-        mma_bf16(d[mt], AH, bl[ks][0], bl[ks][1]);
-        mma_bf16(d[mt], AH, bh[ks][0], bh[ks][1]);
+        // part q of the matrix fragment
+        auto A = [&](int q) {
+          const uint32_t* a = &M.a[16 * q + (mt * 2 + ks) * 4];
+          return a;
+        };
+        // the products a_i b_j with i + j <= NPART - 1, smallest first
+        auto prod = [&](int i, int j) {
+          const uint32_t* a = A(i);
+          const uint32_t AF[4] = {a[0], a[1], a[2], a[3]};
+          mma_bf16(d[mt], AF, b[ks][0][j], b[ks][1][j]);
+        };
+        if constexpr (NPART == 3) {
+          prod(0, 2);
+          prod(1, 1);
+          prod(2, 0);
+        }
+        prod(1, 0);
+        prod(0, 1);
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+        const uint32_t* a = A(0);
+        const uint32_t AF[4] = {a[0], a[1], a[2], a[3]};
+        mma_bf16(t, AF, b[ks][0][0], b[ks][1][0]);
+        lead(mt, t);
       }
   } else {
     // elements t, t+4, t+8, t+12 of task g
@@ -135,9 +186,19 @@ __device__ __forceinline__ void tc_dft8(const TcMat<MODE>& M, int task0, const L
           const uint32_t b1l = f2tf32(v[kk][1] - __uint_as_float(b1h));
           mma_tf32(d[mt], AL, b0h, b1h);
           mma_tf32(d[mt], AH, b0l, b1l);
+          float t[4] = {0.f, 0.f, 0.f, 0.f};
+          mma_tf32(t, AH, b0h, b1h);
+          lead(mt, t);
+        } else {
+          mma_tf32(d[mt], AH, b0h, b1h);
         }
-        mma_tf32(d[mt], AH, b0h, b1h);
       }
+  }
+  if constexpr (MODE != TC_TF32X1) {
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d[mt][i] = e[mt][i] + d[mt][i];
   }
   // outputs: rows g and g+8 (real in m-tile 0, imaginary in m-tile 1), tasks 2t and 2t+1
   if (g < R) {

@@ -1,5 +1,5 @@
 // Tensor-core DFT variant of the 192x192 tile (2-CTA cluster): TF32x3,
-// BF16x3 and TF32x1 modes.  Also builds the DFT-matrix fragment tables.
+// BF16x3, TF32x1 and BF16x6 modes.  Also builds the DFT-matrix fragment tables.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -57,23 +57,25 @@ void fill_table(int mode, int R, int dir, uint32_t* out) {
   for (int lane = 0; lane < 32; ++lane) {
     const int g = lane / 4, t = lane % 4;
     uint32_t* o = out + lane * kTcLaneWords;
-    if (mode == TC_BF16X3) {
-      // m16n8k16 A fragment: {A[g][2t], A[g][2t+1]}, {A[g+8][..]}, {A[g][2t+8], ..}, {A[g+8][2t+8], ..}
+    if (mode == TC_BF16X3 || mode == TC_BF16X6) {
+      // m16n8k16 A fragment: {A[g][2t], A[g][2t+1]}, {A[g+8][..]}, {A[g][2t+8], ..}, {A[g+8][2t+8], ..};
+      // part q (the rounded remainder of the parts before it) at word 16 q
+      const int parts = mode == TC_BF16X6 ? 3 : 2;
       for (int mt = 0; mt < 2; ++mt)
         for (int ks = 0; ks < 2; ++ks)
           for (int reg = 0; reg < 4; ++reg) {
             const int row = 16 * mt + g + ((reg & 1) ? 8 : 0);
             const int col = 16 * ks + 2 * t + ((reg & 2) ? 8 : 0);
-            uint32_t hi = 0, lo = 0;
+            uint32_t w[3] = {0, 0, 0};
             for (int h = 0; h < 2; ++h) {
-              const double v = dft_real(R, dir, row, col + h);
-              const uint16_t bh = to_bf16((float)v);
-              const uint16_t bl = to_bf16((float)(v - (double)bf16_to_f32(bh)));
-              hi |= (uint32_t)bh << (16 * h);
-              lo |= (uint32_t)bl << (16 * h);
+              double v = dft_real(R, dir, row, col + h);
+              for (int q = 0; q < parts; ++q) {
+                const uint16_t b = to_bf16((float)v);
+                v -= (double)bf16_to_f32(b);
+                w[q] |= (uint32_t)b << (16 * h);
+              }
             }
-            o[(mt * 2 + ks) * 4 + reg] = hi;
-            o[16 + (mt * 2 + ks) * 4 + reg] = lo;
+            for (int q = 0; q < parts; ++q) o[16 * q + (mt * 2 + ks) * 4 + reg] = w[q];
           }
     } else {
       // m16n8k8 A fragment: A[g][t], A[g+8][t], A[g][t+4], A[g+8][t+4]
@@ -102,9 +104,9 @@ cudaError_t ensure_tables(int R1, int R2) {
   unsigned long long id = 0;
   if (ptycho::current_context_id(&id) != PTYCHO_OK) return cudaErrorUnknown;
   if (id != 0 && g_ready.count(id)) return cudaSuccess;
-  std::vector<uint32_t> h((size_t)3 * 4 * kTcTableWords, 0u);
-  const int modes[3] = {TC_TF32X3, TC_BF16X3, TC_TF32X1};
-  for (int mi = 0; mi < 3; ++mi)
+  std::vector<uint32_t> h((size_t)kTcModes * 4 * kTcTableWords, 0u);
+  const int modes[kTcModes] = {TC_TF32X3, TC_BF16X3, TC_TF32X1, TC_BF16X6};
+  for (int mi = 0; mi < kTcModes; ++mi)
     for (int m = 0; m < 4; ++m)
       fill_table(modes[mi], m < 2 ? R1 : R2, (m & 1) ? +1 : -1, &h[((size_t)mi * 4 + m) * kTcTableWords]);
   const cudaError_t e = cudaMemcpyToSymbol(g_tc_tables, h.data(), h.size() * 4);
@@ -163,6 +165,7 @@ const EngineOps* engine_192_tc(int mode) {
     case TC_TF32X3: return TcEngine<TC_TF32X3>::ops();
     case TC_BF16X3: return TcEngine<TC_BF16X3>::ops();
     case TC_TF32X1: return TcEngine<TC_TF32X1>::ops();
+    case TC_BF16X6: return TcEngine<TC_BF16X6>::ops();
     default: return nullptr;
   }
 }

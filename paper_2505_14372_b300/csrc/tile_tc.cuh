@@ -14,7 +14,7 @@ namespace ptycho {
 // 1: R1 inverse, 2: R2 forward, 3: R2 inverse (filled once per device by the
 // host).  Defined here: only the tensor-core translation unit includes this.
 constexpr int kTcTableWords = 32 * 64;
-__device__ uint32_t g_tc_tables[3][4][kTcTableWords];
+__device__ uint32_t g_tc_tables[kTcModes][4][kTcTableWords];
 
 template <class Base, int MODE>
 struct TileTC : Base {
