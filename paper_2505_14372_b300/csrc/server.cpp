@@ -201,7 +201,10 @@ int ptycho_server::admit(Request* r) {
       C.ps = ptycho::pos_scratch_at(C.pos_mem, g.h, kPosModes, kMaxSlices);
       slot_bytes += pb;
       // the launches' work queue starts empty (each launch leaves it so)
-      if (cudaMemsetAsync(C.ps.queue, 0, 2 * sizeof(unsigned), C.stream) != cudaSuccess) return PTYCHO_ECUDA;
+      if (cudaMemsetAsync(C.ps.queue, 0, 2 * sizeof(unsigned), C.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PTYCHO_ECUDA;
+      }
     } else {
       cudaGetLastError();
       C.pos_mem = nullptr;
