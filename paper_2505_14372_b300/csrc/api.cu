@@ -212,7 +212,8 @@ struct Timed {
   cudaStream_t s;
   int kid = -1;
   cudaEvent_t a = nullptr;
-  Timed(ptycho_ctx* ctx, const char* name, cudaStream_t st) : c(ctx), s(st) {
+  ptycho::Range range;
+  Timed(ptycho_ctx* ctx, const char* name, cudaStream_t st) : c(ctx), s(st), range(name) {
     if (!c->timing) return;
     if (c->timing == 2 && std::strcmp(name, "adjoint") != 0 && std::strcmp(name, "forward") != 0) return;
     kid = kernel_id(c, name);
@@ -581,6 +582,7 @@ size_t ptycho_scratch_bytes(const ptycho_geom* geom, int32_t B, int32_t waves) {
 
 int ptycho_forward(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
                    float* I_out, ptycho_stream stream) {
+  ptycho::Range range("ptycho_forward");
   int rc = check_call(c, B);
   if (rc) return rc;
   if (B == 0) return PTYCHO_OK;
@@ -614,6 +616,7 @@ int ptycho_forward(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, cons
 int ptycho_adjoint(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
                    const float* I_exp, double* loss_out, ptycho_c64* gO, ptycho_c64* gP, int32_t accumulate,
                    ptycho_stream stream) {
+  ptycho::Range range("ptycho_adjoint");
   int rc = check_call(c, B);
   if (rc) return rc;
   if (!O || !P || (B > 0 && (!pos || !I_exp)) || !gO || !gP) return perr(PTYCHO_EINVAL, "NULL array argument");
@@ -632,6 +635,7 @@ int ptycho_adjoint(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, cons
 int ptycho_adjoint_positions(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
                              const float* I_exp, double* loss_out, ptycho_c64* gO, ptycho_c64* gP, double* gpos_out,
                              int32_t accumulate, ptycho_stream stream) {
+  ptycho::Range range("ptycho_adjoint_positions");
   int rc = check_call(c, B);
   if (rc) return rc;
   if (!O || !P || (B > 0 && (!pos || !I_exp || !gpos_out)) || !gO || !gP)
@@ -649,6 +653,7 @@ int ptycho_adjoint_positions(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c6
 
 int ptycho_vjp(ptycho_ctx* c, const ptycho_c64* O, const ptycho_c64* P, const float* pos, int32_t B,
                const float* gI, ptycho_c64* gO, ptycho_c64* gP, int32_t accumulate, ptycho_stream stream) {
+  ptycho::Range range("ptycho_vjp");
   int rc = check_call(c, B);
   if (rc) return rc;
   if (!O || !P || (B > 0 && (!pos || !gI)) || !gO || !gP) return perr(PTYCHO_EINVAL, "NULL array argument");
@@ -759,6 +764,7 @@ static int step_impl(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
 int ptycho_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* st, const ptycho_opt* opt,
                 const float* pos_all, const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B,
                 double* stats_out, ptycho_stream stream) {
+  ptycho::Range range("ptycho_step");
   int rc = check_call(c, B);
   if (rc) return rc;
   if (B > 0 && !idx) return perr(PTYCHO_EINVAL, "idx is NULL");
@@ -769,6 +775,7 @@ int ptycho_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* st, co
 int ptycho_step_host(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* st, const ptycho_opt* opt,
                      const float* pos_host, const float* I_exp_host, int32_t B, double* loss_host,
                      double* gnorm_host, ptycho_stream stream) {
+  ptycho::Range range("ptycho_step_host");
   int rc = check_call(c, B);
   if (rc) return rc;
   if (B > 0 && (!pos_host || !I_exp_host)) return perr(PTYCHO_EINVAL, "NULL host arrays");
@@ -822,6 +829,7 @@ int ptycho_step_host(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, ptycho_adam* s
 int ptycho_epie_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, float beta_O, float beta_P, const float* pos_all,
                      const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B, double* loss_out,
                      ptycho_stream stream) {
+  ptycho::Range range("ptycho_epie_step");
   int rc = check_call(c, B);
   if (rc) return rc;
   if (!O || !P) return perr(PTYCHO_EINVAL, "NULL object or probe");
@@ -854,6 +862,7 @@ int ptycho_lsqml_step(ptycho_ctx* c, ptycho_c64* O, ptycho_c64* P, const ptycho_
                       const float* illum_prev, const float* trans_prev, float* illum_acc, float* trans_acc,
                       const float* pos_all, const float* I_exp_all, int32_t n_pos, const int32_t* idx, int32_t B,
                       double* loss_out, ptycho_stream stream) {
+  ptycho::Range range("ptycho_lsqml_step");
   int rc = check_call(c, B);
   if (rc) return rc;
   if (!O || !P || !opt) return perr(PTYCHO_EINVAL, "NULL object, probe or options");
@@ -1030,6 +1039,7 @@ int ptycho_kernel_times(ptycho_ctx* c, const char** names, double* ms, int32_t* 
 }
 
 int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count, ptycho_stream stream) {
+  ptycho::Range range("ptycho_fft2");
   const EngineOps* ops = ptycho::engine_for(N);
   if (!ops) return perr(PTYCHO_EINVAL, "N not in {64, 128, 192, 256}");
   if (dir == 0 || count < 0 || (count > 0 && (!in || !out))) return perr(PTYCHO_EINVAL, "bad arguments");
@@ -1041,6 +1051,7 @@ int ptycho_fft2(int32_t N, int32_t dir, const ptycho_c64* in, ptycho_c64* out, i
 
 int ptycho_fft2_dft(int32_t N, int32_t dft, int32_t dir, const ptycho_c64* in, ptycho_c64* out, int32_t count,
                     ptycho_stream stream) {
+  ptycho::Range range("ptycho_fft2_dft");
   if (dft < 0 || dft > 4) return perr(PTYCHO_EINVAL, "unknown dft mode");
   const EngineOps* ops = ptycho::engine_for(N, dft);
   if (!ops) return perr(PTYCHO_EINVAL, "no tile for this N and dft mode");

@@ -2,12 +2,23 @@
 // runtime (server.cpp).  Not part of the C-ABI.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
 #include "ptycho.h"
 
 namespace ptycho {
+
+// Named NVTX range over the lifetime of the object: the library's entry
+// points and kernel launches show by name on the timelines of profilers
+// that collect NVTX (a pointer check when none is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // Host checks of a geometry (dimensions, window size, DFT mode, physics
 // parameters, noise model, waves mode, storage format, object size);

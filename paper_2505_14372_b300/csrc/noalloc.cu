@@ -120,6 +120,7 @@ __global__ void k_static_chirp_table(float2* Hc, const __grid_constant__ Gaps ga
 
 extern "C" int ptycho_forward_static(const ptycho_geom* g, const ptycho_c64* O, const ptycho_c64* P, const float* pos,
                                      int32_t B, float* I_out, uint32_t* status_out, ptycho_stream stream) {
+  ptycho::Range range("ptycho_forward_static");
   int rc = ptycho::validate_geom(g);
   if (rc) return rc;
   if (g->S - 1 > kMaxStaticGaps)

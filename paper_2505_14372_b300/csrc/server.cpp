@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -380,6 +381,9 @@ bool ptycho_server::issue_ticks() {
     }
     if (jobs.empty()) continue;
     int tl = 0;
+    char rn[64];
+    std::snprintf(rn, sizeof rn, "serve tick: window %d, %d jobs", mine.front()->req.geom.h, (int)jobs.size());
+    ptycho::Range range(rn);
     int rc = ptycho::step_batch(jobs.data(), (int)jobs.size(), C.slots, C.nslots, C.stride,
                                 C.pos_mem ? &C.ps : nullptr, status, C.stream, &tl);
     if (rc == PTYCHO_OK && cudaEventCreate(&tk.ev) == cudaSuccess && cudaEventRecord(tk.ev, C.stream) == cudaSuccess) {
