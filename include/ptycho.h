@@ -60,6 +60,7 @@ extern "C" {
 #define PTYCHO_ETIMEDOUT (-5)    /* a bounded wait ran out */
 #define PTYCHO_EBUSY (-6)        /* request not finished / server busy */
 #define PTYCHO_ENOTFOUND (-7)    /* unknown ticket */
+#define PTYCHO_ECHECK (-8)       /* checked build only: an index check failed (a library bug) */
 /* bits of a device status word (ptycho_forward_static's status_out) */
 #define PTYCHO_STATUS_BIT_OUT_OF_BOUNDS 1u /* a scan window left the object; its item was skipped */
 
@@ -304,7 +305,12 @@ int ptycho_lsqml_step(ptycho_ctx* ctx, ptycho_c64* O, ptycho_c64* P, const ptych
                       double* loss_out, ptycho_stream stream);
 
 /* Synchronises `stream` and reports (then clears) the device status word:
- * PTYCHO_EOUTOFBOUNDS if any item was skipped since the last check. */
+ * PTYCHO_EOUTOFBOUNDS if any item was skipped since the last check.  In the
+ * checked build (libptycho_checked.so, see ptycho_build_checked) it first
+ * reports PTYCHO_ECHECK if an index check of this context's window size
+ * failed since the last check (the access was skipped; the results are not
+ * valid): a shared-memory slot outside the wavefield, a window coordinate
+ * outside [0, N) or an item outside its problem. */
 int ptycho_check(ptycho_ctx* ctx, ptycho_stream stream);
 
 /* Grouping (§2.2): writes a permutation of 0..P-1 into out_idx[P] (host)
@@ -470,6 +476,11 @@ uint64_t ptycho_kernels_launched(void);
 
 const char* ptycho_last_error(void);
 const char* ptycho_version(void);
+/* 1 in the checked build (libptycho_checked.so: the same entry points, with
+ * index checks in the kernels that record a bit and skip the access instead
+ * of trapping, reported by ptycho_check as PTYCHO_ECHECK), 0 in the normal
+ * build.  The paper has no counterpart: a debugging aid. */
+int32_t ptycho_build_checked(void);
 
 #ifdef __cplusplus
 }

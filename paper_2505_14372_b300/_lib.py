@@ -10,11 +10,14 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libptycho.so")
+# PTYCHO_LIBRARY=checked loads the checked build (libptycho_checked.so: the
+# same entry points with index checks in the kernels)
+LIB_PATH = os.path.join(HERE, "libptycho_checked.so" if os.environ.get("PTYCHO_LIBRARY") == "checked"
+                        else "libptycho.so")
 
-OK, EINVAL, EOUTOFBOUNDS, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, EOUTOFBOUNDS, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, ENOTFOUND, ECHECK = 0, -1, -2, -3, -4, -5, -6, -7, -8
 ERR_NAMES = {EINVAL: "EINVAL", EOUTOFBOUNDS: "EOUTOFBOUNDS", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
-             ETIMEDOUT: "ETIMEDOUT", EBUSY: "EBUSY", ENOTFOUND: "ENOTFOUND"}
+             ETIMEDOUT: "ETIMEDOUT", EBUSY: "EBUSY", ENOTFOUND: "ENOTFOUND", ECHECK: "ECHECK"}
 
 
 class PtychoError(RuntimeError):
@@ -110,6 +113,7 @@ SIGNATURES = {
     "ptycho_kernels_launched": (C.c_uint64, []),
     "ptycho_last_error": (C.c_char_p, []),
     "ptycho_version": (C.c_char_p, []),
+    "ptycho_build_checked": (C.c_int32, []),
 }
 
 _lib = None

@@ -996,6 +996,9 @@ int ptycho_check(ptycho_ctx* c, ptycho_stream stream) {
   unsigned st = 0;
   CK(cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost));
   CK(cudaMemset(c->status, 0, sizeof(unsigned)));
+  if (const unsigned bits = c->ops->take_check_bits())
+    return perr(PTYCHO_ECHECK, "checked build: an index check failed (bits " + std::to_string(bits) +
+                                   ": 1 shared-memory slot, 2 window coordinate, 4 item); the access was skipped");
   if (c->ops->take_exchange_timeouts())
     return perr(PTYCHO_ETIMEDOUT, "a bounded wait of the cluster exchange ran out; the last results are not valid");
   if (st & ptycho::PTYCHO_STATUS_OUT_OF_BOUNDS)
@@ -1089,6 +1092,7 @@ int ptycho_set_step_counter(ptycho_ctx* c, int64_t* t_dev) {
 }
 
 const char* ptycho_version(void) { return "libptycho 0.1 (sm_103a)"; }
+int32_t ptycho_build_checked(void) { return PTYCHO_CHECKED ? 1 : 0; }
 
 }  // extern "C"
 

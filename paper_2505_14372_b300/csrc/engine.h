@@ -36,6 +36,9 @@ struct EngineOps {
   // not available for this tile)
   cudaError_t (*step_tail)(const TailArgs& A, int blocks, cudaStream_t s);
   int (*tail_blocks)(long long nO, int K);
+  // checked build (check.cuh): index-check bits of this tile's kernels since
+  // the last call, read and cleared (always 0 in the normal build)
+  unsigned (*take_check_bits)();
 };
 
 const EngineOps* engine_64();
@@ -43,7 +46,7 @@ const EngineOps* engine_128();
 const EngineOps* engine_192();
 const EngineOps* engine_256();
 
-// tensor-core DFT variants (mode 1 TF32x3, 2 BF16x3, 3 TF32x1), 192x192 only
+// tensor-core DFT variants (mode 1 TF32x3, 2 BF16x3, 3 TF32x1, 4 BF16x6), 192x192 only
 const EngineOps* engine_192_tc(int mode);
 
 inline const EngineOps* engine_for(int N, int dft = 0) {

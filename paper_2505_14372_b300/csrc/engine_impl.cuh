@@ -192,6 +192,25 @@ struct Engine {
     return v;
   }
 
+  // checked build: index-check bits of this tile's kernels since the last
+  // call (read and cleared); always 0 in the normal build
+  static unsigned take_check_bits() {
+#if PTYCHO_CHECKED
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_check_bits, sizeof(v)) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    if (v) {
+      const unsigned z = 0;
+      if (cudaMemcpyToSymbol(g_check_bits, &z, sizeof(z)) != cudaSuccess) cudaGetLastError();
+    }
+    return v;
+#else
+    return 0;
+#endif
+  }
+
   static cudaError_t step_tail(const TailArgs& A, int blocks, cudaStream_t s) {
     if constexpr (TL::G == 1) return launch_ex(k_step_tail<TL>, blocks, true, s, A);
     else return cudaErrorNotSupported;
@@ -216,7 +235,7 @@ struct Engine {
                                 TL::SMEM,      &probe_spectrum, &forward, &adjoint,  &probe_grad,
                                 &fft_debug,    &modesum,   &loss,       &seed,       &resident_clusters,
                                 &adjoint_pos,  &resident_pos, &take_exchange_timeouts, &exchange_probe, ALLV,
-                                &step_tail,    &tail_blocks};
+                                &step_tail,    &tail_blocks, &take_check_bits};
     return &o;
   }
 };

@@ -8,6 +8,11 @@
 
 #include "ptycho.h"
 
+// 1 in the checked build (check.cuh)
+#ifndef PTYCHO_CHECKED
+#define PTYCHO_CHECKED 0
+#endif
+
 namespace ptycho {
 
 // Named NVTX range over the lifetime of the object: the library's entry

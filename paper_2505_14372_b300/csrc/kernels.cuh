@@ -113,6 +113,13 @@ __device__ __forceinline__ ItemGeo item_geo(const ProblemDesc& D, int item) {
   const int local = item - D.item0;
   g.j = local / D.K;
   g.k = local - g.j * D.K;
+  if (!chk(local >= 0 && g.j < D.B, kChkItem)) {  // checked build: an item outside its problem
+    g.j = g.k = g.jj = 0;
+    g.ok = false;
+    g.ny = g.nx = 0;
+    g.dy = g.dx = 0.0;
+    return g;
+  }
   g.jj = D.idx ? D.idx[g.j] : g.j;
   if (g.jj < 0 || g.jj >= D.npos) {
     g.ok = false;

@@ -45,6 +45,7 @@
 #pragma once
 #include <stdint.h>
 
+#include "check.cuh"
 #include "radix.cuh"
 
 namespace ptycho {
@@ -209,7 +210,8 @@ struct Tile {
       base = G == 1 ? 0 : b * BLK;
       f = (R1 * r + NB * b + cc / R2) & 7;
     }
-    return base + r * ROWS + (((cc >> 1) ^ f) << 1) + (cc & 1);
+    const int idx = base + r * ROWS + (((cc >> 1) ^ f) << 1) + (cc & 1);
+    return chk(idx >= 0 && idx < WAVE, kChkSmem) ? idx : 0;
   }
   // 16-byte pair (slots s, s + 1) holding columns cc, cc + 1 (cc even)
   __device__ static __forceinline__ void ld_pair(const float2* wave, int s, float2& a, float2& b) {
@@ -349,6 +351,7 @@ struct Tile {
       if (TS % T != 0 && id >= TS) break;
       const int r = id / R2, n2 = id % R2;
       const int grow = rank * ROWS + r;
+      if (!chk(id >= 0 && grow < N && n2 + R2 * (R1 - 1) < N, kChkWindow)) continue;
       typename Pre::type pv[R1];
 #pragma unroll
       for (int i = 0; i < R1; ++i) pv[i] = pre(grow, n2 + R2 * i);
@@ -565,6 +568,7 @@ struct Tile {
       const int b = k1 / NB, r0 = R2 * (k1 % NB);
       const int pv = rank * ROWS + cc;
       const int pu0 = R2 * k1;
+      if (!chk(pv >= 0 && pv < N && pu0 >= 0 && pu0 + R2 <= N, kChkWindow)) continue;
       float2 x[R2];
       if constexpr (FROM_SMEM) {
 #pragma unroll

@@ -68,7 +68,7 @@ struct TileTC : Base {
               } else {
                 const int r = id / R2, col = id % R2 + R2 * m;
                 const int grow = rank * ROWS + r;
-                op(grow, col, v, pre(grow, col));
+                if (chk(grow >= 0 && grow < N && col < N, kChkWindow)) op(grow, col, v, pre(grow, col));
               }
             });
         if constexpr (TO_SMEM) __syncwarp();
@@ -79,7 +79,8 @@ struct TileTC : Base {
             [&](int id, int e) {
               const int r = id / R2, col = id % R2 + R2 * e;
               const int grow = rank * ROWS + r;
-              float2 v;
+              float2 v = make_float2(0.f, 0.f);
+              if (!chk(grow >= 0 && grow < N && col < N, kChkWindow)) return v;
               if constexpr (FROM_SMEM) v = wave[sl(id, e)];
               else v = load(grow, col);
               op(grow, col, v, pre(grow, col));
@@ -189,7 +190,7 @@ struct TileTC : Base {
               } else {
                 int pu, pv;
                 pu_pv(id, m, pu, pv);
-                op(pu, pv, v);
+                if (chk(pu >= 0 && pu < N && pv >= 0 && pv < N, kChkWindow)) op(pu, pv, v);
                 if constexpr (WB) wave[sl(id, m)] = v;
               }
             });
@@ -201,7 +202,8 @@ struct TileTC : Base {
             [&](int id, int e) {
               int pu, pv;
               pu_pv(id, e, pu, pv);
-              float2 v;
+              float2 v = make_float2(0.f, 0.f);
+              if (!chk(pu >= 0 && pu < N && pv >= 0 && pv < N, kChkWindow)) return v;
               if constexpr (FWD || FROM_SMEM) v = wave[sl(id, e)];
               else v = load(pu, pv);
               op(pu, pv, v);

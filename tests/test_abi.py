@@ -143,3 +143,18 @@ def test_deterministic_flag_validation():
     g, _dz = Geometry(S=1, K=1, N=64, H=80, W=80).to_c()
     g.deterministic = 2
     assert lib.ptycho_create(C.byref(g), 4, 0, C.byref(h)) == _lib.EINVAL
+
+
+def test_checked_build_exports_the_same_entry_points():
+    """The checked build (index checks in the kernels, PTYCHO_ECHECK) is the
+    same C-ABI: every symbol of the normal library, and ptycho_build_checked
+    telling the two apart (host-only calls, no GPU needed)."""
+    here = os.path.join(ROOT, "paper_2505_14372_b300")
+    normal, checked = os.path.join(here, "libptycho.so"), os.path.join(here, "libptycho_checked.so")
+    assert os.path.exists(checked), "build it with python -m paper_2505_14372_b300.build --checked"
+    ln, lc = C.CDLL(normal), C.CDLL(checked)
+    missing = [n for n in declared_functions() if not hasattr(lc, n)]
+    assert not missing, missing
+    ln.ptycho_build_checked.restype = C.c_int32
+    lc.ptycho_build_checked.restype = C.c_int32
+    assert ln.ptycho_build_checked() == 0 and lc.ptycho_build_checked() == 1
