@@ -61,6 +61,8 @@ extern "C" {
 #define PTYCHO_EBUSY (-6)        /* request not finished / server busy */
 #define PTYCHO_ENOTFOUND (-7)    /* unknown ticket */
 #define PTYCHO_ECHECK (-8)       /* checked build only: an index check failed (a library bug) */
+#define PTYCHO_ECANCELED (-9)    /* served request cancelled (ptycho_cancel) */
+#define PTYCHO_ENONFINITE (-10)  /* served request's loss became non-finite (it diverged) */
 /* bits of a device status word (ptycho_forward_static's status_out) */
 #define PTYCHO_STATUS_BIT_OUT_OF_BOUNDS 1u /* a scan window left the object; its item was skipped */
 
@@ -442,7 +444,10 @@ typedef struct {
 int ptycho_server_create(size_t hbm_budget_bytes, int32_t max_active, ptycho_server** out);
 int ptycho_server_destroy(ptycho_server* srv); /* cancels unfinished work */
 /* Non-blocking; copies the request's host arrays.  ENOMEM if the request
- * alone exceeds the budget.  Served requests take 1 <= S <= 32 slices (the
+ * alone exceeds the budget; EINVAL for a geometry ptycho_create would
+ * refuse, and for a non-finite value in the positions, patterns, probe or
+ * object (the message names the first one); EOUTOFBOUNDS for a scan
+ * position whose window leaves the object.  Served requests take 1 <= S <= 32 slices (the
  * per-window-size slot scratch is sized for 32; EINVAL beyond), the FFT
  * tile, FP32 entry waves and the atomic gradient sums; those with K <= 8
  * modes ride in the shared position-major launch of their window size,
@@ -453,6 +458,19 @@ int ptycho_poll(ptycho_server* srv, uint64_t ticket, ptycho_status* st, ptycho_r
 /* Blocks until the ticket is DONE/FAILED or timeout_ms passes (ETIMEDOUT). */
 int ptycho_wait(ptycho_server* srv, uint64_t ticket, double timeout_ms);
 int ptycho_release(ptycho_server* srv, uint64_t ticket);
+/* Cancels a request: a queued one ends at once; an admitted one gets no
+ * further step, and once the steps already enqueued for it are done its
+ * device state is freed.  Either way it ends FAILED with error
+ * PTYCHO_ECANCELED (ptycho_poll / ptycho_wait show it; release it as usual).
+ * No effect on a request that has already ended.  The other requests are
+ * not affected.  A served request whose loss turns non-finite (checked at
+ * the end of every iteration) ends the same way with PTYCHO_ENONFINITE. */
+int ptycho_cancel(ptycho_server* srv, uint64_t ticket);
+/* Host-side fault injection for tests (the paper has no counterpart): the
+ * server's worker thread sleeps `ms` milliseconds before its next tick, as
+ * a stalled worker would, so that clients' time-outs (ptycho_wait) can be
+ * exercised.  Nothing is done to the GPU. */
+int ptycho_server_inject_stall(ptycho_server* srv, double ms);
 int ptycho_server_stats_get(ptycho_server* srv, ptycho_server_stats* out);
 
 /* FP32 CUDA-core throughput microbenchmark (measurement support: the

@@ -16,8 +16,10 @@ LIB_PATH = os.path.join(HERE, "libptycho_checked.so" if os.environ.get("PTYCHO_L
                         else "libptycho.so")
 
 OK, EINVAL, EOUTOFBOUNDS, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, ENOTFOUND, ECHECK = 0, -1, -2, -3, -4, -5, -6, -7, -8
+ECANCELED, ENONFINITE = -9, -10
 ERR_NAMES = {EINVAL: "EINVAL", EOUTOFBOUNDS: "EOUTOFBOUNDS", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
-             ETIMEDOUT: "ETIMEDOUT", EBUSY: "EBUSY", ENOTFOUND: "ENOTFOUND", ECHECK: "ECHECK"}
+             ETIMEDOUT: "ETIMEDOUT", EBUSY: "EBUSY", ENOTFOUND: "ENOTFOUND", ECHECK: "ECHECK",
+             ECANCELED: "ECANCELED", ENONFINITE: "ENONFINITE"}
 
 
 class PtychoError(RuntimeError):
@@ -107,6 +109,8 @@ SIGNATURES = {
     "ptycho_poll": (I32, [P_, C.c_uint64, C.POINTER(Status), C.POINTER(Result)]),
     "ptycho_wait": (I32, [P_, C.c_uint64, C.c_double]),
     "ptycho_release": (I32, [P_, C.c_uint64]),
+    "ptycho_cancel": (I32, [P_, C.c_uint64]),
+    "ptycho_server_inject_stall": (I32, [P_, C.c_double]),
     "ptycho_server_stats_get": (I32, [P_, C.POINTER(ServerStats)]),
     "ptycho_fp32_peak_launch": (I32, [I32, I32, P_, C.POINTER(C.c_double), P_]),
     "ptycho_fp32_peak_sink_elems": (I32, []),

@@ -342,6 +342,14 @@ class Server:
     def release(self, ticket: int):
         check(lib().ptycho_release(self.h, ticket))
 
+    def cancel(self, ticket: int):
+        """Ends the request (FAILED, error ECANCELED) without disturbing the others."""
+        check(lib().ptycho_cancel(self.h, ticket))
+
+    def inject_stall(self, ms: float):
+        """Fault injection for tests: the worker sleeps `ms` before its next tick."""
+        check(lib().ptycho_server_inject_stall(self.h, float(ms)))
+
     def stats(self) -> dict:
         s = _lib.ServerStats()
         check(lib().ptycho_server_stats_get(self.h, C.byref(s)))

@@ -74,6 +74,13 @@ struct Request {
   double last_iter_ms = -1;
   int iterations_done = 0;
   double last_loss = 0;
+  // stopping: non-zero once the request is to end without finishing
+  // (PTYCHO_ECANCELED, PTYCHO_ENONFINITE); no new steps are issued for it,
+  // and it fails once none of its ticks is in flight
+  int stop_code = 0;
+  int inflight = 0;                 // ticks in flight that include it
+  double* iter_loss = nullptr;      // pinned host [iterations]: loss of each iteration's last step
+
   // results
   std::vector<ptycho_c64> O_out, P_out;
   std::vector<double> loss_out, step_ms, iter_ms;
@@ -146,6 +153,7 @@ struct ptycho_server {
   int64_t n_submitted = 0, n_admitted = 0, n_finished = 0, n_failed = 0, n_launches = 0;
   double positions_done = 0, first_start_ms = -1, last_end_ms = -1;
   std::vector<double> iter_lat;
+  double stall_ms = 0;  // host-side fault injection: the worker sleeps this long before its next tick
 
   void run();
   int admit(Request* r);
@@ -168,6 +176,8 @@ void ptycho_server::release_device(Request* r) {
   r->dstats = nullptr;
   if (r->start_ev) cudaEventDestroy(r->start_ev);
   r->start_ev = nullptr;
+  if (r->iter_loss) cudaFreeHost(r->iter_loss);
+  r->iter_loss = nullptr;
 }
 
 void ptycho_server::fail(Request* r, int code) {
@@ -224,7 +234,8 @@ int ptycho_server::admit(Request* r) {
             cudaMalloc(&r->mP, nP * 8) == cudaSuccess && cudaMalloc(&r->vP, nP * 4) == cudaSuccess &&
             cudaMalloc(&r->dpos, (size_t)n * 8) == cudaSuccess && cudaMalloc(&r->dI, (size_t)n * NP * 4) == cudaSuccess &&
             cudaMalloc(&r->didx, (size_t)n * 8) == cudaSuccess &&
-            cudaMalloc(&r->dstats, (size_t)r->total_steps * 16) == cudaSuccess;
+            cudaMalloc(&r->dstats, (size_t)r->total_steps * 16) == cudaSuccess &&
+            cudaMallocHost(&r->iter_loss, (size_t)r->req.iterations * 8) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return PTYCHO_ENOMEM;
@@ -283,6 +294,7 @@ bool ptycho_server::retire_ticks() {
       Tick& tk = C.inflight.front();
       const cudaError_t q = cudaEventQuery(tk.ev);
       if (q == cudaErrorNotReady) break;
+      for (auto& w : tk.who) w.first->inflight -= 1;
       if (q != cudaSuccess) {
         cudaGetLastError();
         for (auto& w : tk.who)
@@ -297,6 +309,10 @@ bool ptycho_server::retire_ticks() {
           if (r->state != PTYCHO_REQ_RUNNING) continue;
           r->steps_done += 1;
           if (w.second) {
+            // the loss of the iteration's last step (copied after it): a
+            // non-finite value ends the request (diverged, or data the
+            // submit checks could not see through)
+            if (!std::isfinite(r->iter_loss[r->iterations_done]) && !r->stop_code) r->stop_code = PTYCHO_ENONFINITE;
             double t_prev = r->last_iter_ms;
             if (t_prev < 0) {
               float ts = 0.f;
@@ -315,11 +331,16 @@ bool ptycho_server::retire_ticks() {
       any = true;
     }
   }
-  for (Request* r : std::vector<Request*>(active))
-    if (r->state == PTYCHO_REQ_RUNNING && r->steps_done == r->total_steps) {
+  for (Request* r : std::vector<Request*>(active)) {
+    if (r->state != PTYCHO_REQ_RUNNING) continue;
+    if (r->stop_code && r->inflight == 0) {  // nothing of it left on the device
+      fail(r, r->stop_code);
+      any = true;
+    } else if (!r->stop_code && r->steps_done == r->total_steps) {
       finish(r);
       any = true;
     }
+  }
   return any;
 }
 
@@ -332,7 +353,8 @@ bool ptycho_server::issue_ticks() {
     if (!C.stream || (int)C.inflight.size() >= kMaxInflight) continue;
     std::vector<Request*> mine;
     for (Request* r : active)
-      if (r->cls == k && r->state == PTYCHO_REQ_RUNNING && r->steps_issued < r->total_steps) mine.push_back(r);
+      if (r->cls == k && r->state == PTYCHO_REQ_RUNNING && !r->stop_code && r->steps_issued < r->total_steps)
+        mine.push_back(r);
     if (mine.empty()) continue;
     if (mine.size() > (size_t)ptycho::kMaxDesc) {
       std::rotate(mine.begin(), mine.begin() + (C.rr % mine.size()), mine.end());
@@ -341,6 +363,7 @@ bool ptycho_server::issue_ticks() {
     }
     std::vector<StepJob> jobs;
     Tick tk;
+    std::vector<std::pair<double*, const double*>> loss_copies;  // (pinned host, device) per closed iteration
     for (Request* r : mine) {
       const int n = r->req.n_pos, B = r->req.batch;
       if (r->group == 0) {
@@ -373,6 +396,7 @@ bool ptycho_server::issue_ticks() {
       bool closes = false;
       r->steps_issued += 1;
       if (++r->group == r->groups) {
+        loss_copies.push_back({r->iter_loss + r->iteration, J.stats});
         r->group = 0;
         r->iteration += 1;
         closes = true;
@@ -386,7 +410,12 @@ bool ptycho_server::issue_ticks() {
     ptycho::Range range(rn);
     int rc = ptycho::step_batch(jobs.data(), (int)jobs.size(), C.slots, C.nslots, C.stride,
                                 C.pos_mem ? &C.ps : nullptr, status, C.stream, &tl);
+    for (const auto& lc : loss_copies)
+      if (rc == PTYCHO_OK && cudaMemcpyAsync(lc.first, lc.second, sizeof(double), cudaMemcpyDeviceToHost, C.stream) !=
+                                 cudaSuccess)
+        rc = PTYCHO_ECUDA;
     if (rc == PTYCHO_OK && cudaEventCreate(&tk.ev) == cudaSuccess && cudaEventRecord(tk.ev, C.stream) == cudaSuccess) {
+      for (auto& w : tk.who) w.first->inflight += 1;
       C.inflight.push_back(tk);
       n_launches += tl;
       any = true;
@@ -402,6 +431,14 @@ void ptycho_server::run() {
   cudaSetDevice(device);
   std::unique_lock<std::mutex> lk(mu);
   while (!stop) {
+    if (stall_ms > 0) {  // injected stall (tests of the clients' time-outs)
+      const double ms = stall_ms;
+      stall_ms = 0;
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds((long long)(ms * 1e3)));
+      lk.lock();
+      continue;
+    }
     // admission: first come, first served, against slots and the HBM budget
     while (!queue.empty() && (int)active.size() < max_active) {
       Request* r = queue.front();
@@ -508,16 +545,24 @@ int ptycho_submit(ptycho_server* s, const ptycho_request* q, uint64_t* ticket) {
     return perr(PTYCHO_EINVAL, "TV regularisers need reg_tv_eps > 0");
   if (g.wave_prec != PTYCHO_PREC_F32) return perr(PTYCHO_EINVAL, "served requests keep FP32 entry waves");
   if (g.deterministic) return perr(PTYCHO_EINVAL, "served requests use the atomic gradient sums (deterministic = 0)");
-  {
-    // host-side validation of the rest of the geometry through a probe context is
-    // not possible without allocating; check the fields the kernels rely on
-    if (!(g.dx > 0) || !(g.lambda > 0)) return perr(PTYCHO_EINVAL, "dx and lambda must be > 0");
-    if (g.loss == PTYCHO_LOSS_POISSON && !(g.eps > 0)) return perr(PTYCHO_EINVAL, "Poisson loss needs eps > 0");
-    if (g.loss == PTYCHO_LOSS_AMPLITUDE && !(g.eps + g.c > 0)) return perr(PTYCHO_EINVAL, "amplitude needs eps + c > 0");
-    if (g.loss != PTYCHO_LOSS_POISSON && g.loss != PTYCHO_LOSS_AMPLITUDE && g.loss != PTYCHO_LOSS_GAUSSIAN)
-      return perr(PTYCHO_EINVAL, "unknown loss");
-    if (g.loss == PTYCHO_LOSS_GAUSSIAN && !(g.c > 0)) return perr(PTYCHO_EINVAL, "Gaussian loss needs c > 0");
-  }
+  if (int rc = ptycho::validate_geom(&g)) return rc;  // the rest of the geometry, as ptycho_create checks it
+  // non-finite data would turn the whole reconstruction into NaN: refuse it
+  // here, with the first offending index
+  auto first_nonfinite = [](const float* a, size_t n) -> long long {
+    for (size_t i = 0; i < n; ++i)
+      if (!std::isfinite(a[i])) return (long long)i;
+    return -1;
+  };
+  const size_t NPq = (size_t)g.h * g.w;
+  if (long long i = first_nonfinite(q->pos, 2 * (size_t)q->n_pos); i >= 0)
+    return perr(PTYCHO_EINVAL, "scan position " + std::to_string(i / 2) + " is not finite");
+  if (long long i = first_nonfinite(q->I_exp, (size_t)q->n_pos * NPq); i >= 0)
+    return perr(PTYCHO_EINVAL, "pattern " + std::to_string(i / (long long)NPq) + " holds a non-finite value");
+  if (long long i = first_nonfinite(&q->P_init[0].re, 2 * (size_t)g.K * NPq); i >= 0)
+    return perr(PTYCHO_EINVAL, "probe mode " + std::to_string(i / (2 * (long long)NPq)) + " holds a non-finite value");
+  if (q->O_init)
+    if (long long i = first_nonfinite(&q->O_init[0].re, 2 * (size_t)g.S * g.H * g.W); i >= 0)
+      return perr(PTYCHO_EINVAL, "object slice " + std::to_string(i / (2LL * g.H * g.W)) + " holds a non-finite value");
   for (int j = 0; j < q->n_pos; ++j) {
     const double y = std::floor((double)q->pos[2 * j] + 0.5), x = std::floor((double)q->pos[2 * j + 1] + 0.5);
     if (!(y >= 0 && x >= 0 && y + g.h <= g.H && x + g.w <= g.W))
@@ -597,6 +642,35 @@ int ptycho_wait(ptycho_server* s, uint64_t ticket, double timeout_ms) {
       return perr(PTYCHO_ETIMEDOUT, "request not finished before the timeout");
     }
   }
+}
+
+int ptycho_cancel(ptycho_server* s, uint64_t ticket) {
+  if (!s) return perr(PTYCHO_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return perr(PTYCHO_ENOTFOUND, "unknown ticket");
+  Request* r = it->second.get();
+  if (r->state == PTYCHO_REQ_QUEUED) {  // never admitted: nothing on the device
+    s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), r), s->queue.end());
+    r->state = PTYCHO_REQ_FAILED;
+    r->error = PTYCHO_ECANCELED;
+    r->finish_ms = host_ms(s->host0);
+    ++s->n_failed;
+  } else if (r->state == PTYCHO_REQ_ADMITTING || r->state == PTYCHO_REQ_RUNNING) {
+    // the worker issues no further step and ends it once its ticks are done
+    if (!r->stop_code) r->stop_code = PTYCHO_ECANCELED;
+  }
+  s->cv.notify_all();
+  return PTYCHO_OK;
+}
+
+int ptycho_server_inject_stall(ptycho_server* s, double ms) {
+  if (!s) return perr(PTYCHO_EINVAL, "server is NULL");
+  if (!(ms >= 0) || !std::isfinite(ms)) return perr(PTYCHO_EINVAL, "stall must be finite and >= 0 ms");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->stall_ms = ms;
+  s->cv.notify_all();
+  return PTYCHO_OK;
 }
 
 int ptycho_release(ptycho_server* s, uint64_t ticket) {
