@@ -1,6 +1,6 @@
 // Small complex DFTs as tensor-core GEMMs (warp-level mma.sync), with the
-// fp32 operands split into two lower-precision terms so that three products
-// recover near-fp32 accuracy (precision variant of the FFT tile).
+// fp32 operands split into lower-precision terms whose largest cross
+// products recover near-fp32 accuracy (precision variant of the FFT tile).
 //
 // One call transforms 8 tasks (vectors of R <= 16 complex values) at once:
 //   Y = M X,  X: 32 x 8 (rows 0-15 real parts, 16-31 imaginary parts of the
