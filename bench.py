@@ -172,7 +172,7 @@ def kernel_source_hash(N):
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_14372_b300", "csrc")
-    for name in ("radix.cuh", "tile.cuh", "kernels.cuh", "elementwise.cuh", "noise.cuh", "launch.h",
+    for name in ("radix.cuh", "check.cuh", "tile.cuh", "kernels.cuh", "elementwise.cuh", "noise.cuh", "launch.h",
                  "engine_impl.cuh", f"tile{N}.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
