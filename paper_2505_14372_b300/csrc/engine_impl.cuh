@@ -152,15 +152,23 @@ struct Engine {
     k_seed<TL><<<blocks, 256, 0, s>>>(gI, B, w);
     return cudaGetLastError();
   }
+  // launches that mix problems (positions of different cost) take their
+  // positions from the work queue; they run the FP32 gradient variant
   static cudaError_t adjoint_pos(const LaunchArgs& L, const PosArgs& F, int clusters, int variant, cudaStream_t s) {
-    if (!F.queue) return cudaErrorInvalidValue;
-    return with_variant<kVarDet>(
-        variant, [&](auto v) { return launch_ex(k_adjoint_pos<TL, decltype(v)::value>, clusters, true, s, L, F); });
+    if constexpr (ALLV) {  // the tiles that serve requests
+      if (L.nd > 1 && variant == kVarF32) {
+        if (!F.queue) return cudaErrorInvalidValue;
+        return launch_ex(k_adjoint_pos<TL, kVarF32, true>, clusters, true, s, L, F);
+      }
+    }
+    return with_variant<kVarDet>(variant, [&](auto v) {
+      return launch_ex(k_adjoint_pos<TL, decltype(v)::value, false>, clusters, true, s, L, F);
+    });
   }
   static int resident_pos(int variant) {
     int n = 0;
     with_variant<kVarDet>(variant, [&](auto v) {
-      n = resident(k_adjoint_pos<TL, decltype(v)::value>);
+      n = resident(k_adjoint_pos<TL, decltype(v)::value, false>);
       return cudaSuccess;
     });
     return n;

@@ -622,21 +622,27 @@ __device__ __forceinline__ void adjoint_position(Smem<TL>& sm, const LaunchArgs&
 // Loss + adjoint with the entry waves recomputed, one cluster per scan
 // position (position-major, one launch per step, no waits between
 // clusters; the positions of several problems of one window size may share
-// a launch).  Cluster c takes entry c of the processing order first; when
-// the launch has more positions than clusters, the rest go through the
-// launch's work queue: a cluster claims the next entry when it finishes a
-// position, so that clusters finishing early take more (positions of
-// different problems cost different amounts: S slices, K modes).  Claims
-// are made at the end of a position rather than ahead of it: an early claim
-// would take work from clusters that have not started yet.  For position j the
-// cluster runs the forward pass of every mode k (entry waves to part k of
-// its slot, far field A_k to its scratch, the intensity summed over modes in
-// its scratch), applies the noise model to the mode sum (loss into lpart[j],
-// seed weight 2 l'(I) / NP in place of I), then runs the backward pass of
-// every mode from the seed w A_k.  Every pixel of the scratch is written and
-// read back by the same thread (the column stage's task mapping), so the
-// scratch needs no synchronisation beyond program order.
-template <class TL, int V>
+// a launch).  For position j the cluster runs the forward pass of every
+// mode k (entry waves to part k of its slot, far field A_k to its scratch,
+// the intensity summed over modes in its scratch), applies the noise model
+// to the mode sum (loss into lpart[j], seed weight 2 l'(I) / NP in place of
+// I), then runs the backward pass of every mode from the seed w A_k.  Every
+// pixel of the scratch is written and read back by the same thread (the
+// column stage's task mapping), so the scratch needs no synchronisation
+// beyond program order.
+//
+// Assignment of positions to clusters.  Without QUEUE (launches of one
+// problem, whose positions all cost the same) cluster c takes entries c,
+// c + clusters, ... of the processing order.  With QUEUE (launches that mix
+// problems: positions cost S slices times K modes of their own problem)
+// cluster c takes entry c first and then claims the next entry from the
+// launch's work queue whenever it finishes a position, so that clusters
+// finishing early take more.  Claims are made at the end of a position
+// rather than ahead of it: an early claim would take work from clusters
+// that have not started yet.  (The queue's loop state costs the kernel 9
+// registers, and launches of one problem 1.2 % of their time, so they keep
+// the static assignment.)
+template <class TL, int V, bool QUEUE>
 __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_constant__ LaunchArgs L,
                                                                  const __grid_constant__ PosArgs F) {
   extern __shared__ float4 smem_raw[];
@@ -647,38 +653,51 @@ __global__ void __launch_bounds__(TL::T, TL::MINB) k_adjoint_pos(const __grid_co
   char* slot = L.slots + (size_t)cid * L.slot_stride;
   float2* Ab = F.Abuf + (size_t)cid * F.astride;
   float* Ib = F.Ibuf + (size_t)cid * TL::NP;
-  // claim word: written at the end of a position, read after the next
-  // cluster barrier, written again only after at least one more (every
-  // position's work holds one: the backward pass of each mode starts with
-  // it, and a skipped position takes one)
-  __shared__ int claim;
-  int it = cid;  // entry of the processing order; < 0: read the claim
   pdl_wait();
+  if constexpr (!QUEUE) {
 #pragma unroll 1
-  for (;;) {
-    // also: the partner CTAs are done with the previous position
-    TL::sync_cluster();
-    if (it < 0) it = n_clusters<TL>() + claim;
-    if (it >= L.total) break;
-    adjoint_position<TL, V>(sm, L, F, rank, it, slot, Ab, Ib);
-    // claim the next entry (or leave when there is no queue)
-    if (L.total > n_clusters<TL>()) {
-      claim_next<TL>(&claim, F.queue, rank);
-      it = -1;
-    } else {
-      it = L.total;
+    for (int it = cid; it < L.total; it += n_clusters<TL>()) {
+      // the partner CTAs are done with the previous position
+      TL::sync_cluster();
+      adjoint_position<TL, V>(sm, L, F, rank, it, slot, Ab, Ib);
     }
-  }
-  pdl_trigger();
-  // no CTA leaves while its partner may still be sending to it
-  TL::sync_cluster();
-  // every cluster made its last claim before counting itself out, so the
-  // last one out can reset the queue for the next launch
-  if (L.total > n_clusters<TL>() && rank == 0 && threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(F.queue + 1, 1u) == (unsigned)n_clusters<TL>() - 1u) {
-      atomicExch(F.queue, 0u);
-      atomicExch(F.queue + 1, 0u);
+    pdl_trigger();
+    // no CTA leaves while its partner may still be sending to it
+    TL::sync_cluster();
+  } else {
+    // claim word: written at the end of a position, read after the next
+    // cluster barrier, written again only after at least one more (every
+    // position's work holds one: the backward pass of each mode starts with
+    // it, and a skipped position takes one)
+    __shared__ int claim;
+    const bool queued = L.total > n_clusters<TL>();
+    int it = cid;  // entry of the processing order; < 0: read the claim
+#pragma unroll 1
+    for (;;) {
+      // also: the partner CTAs are done with the previous position
+      TL::sync_cluster();
+      if (it < 0) it = n_clusters<TL>() + claim;
+      if (it >= L.total) break;
+      adjoint_position<TL, V>(sm, L, F, rank, it, slot, Ab, Ib);
+      // claim the next entry (or leave when every position has its cluster)
+      if (queued) {
+        claim_next<TL>(&claim, F.queue, rank);
+        it = -1;
+      } else {
+        it = L.total;
+      }
+    }
+    pdl_trigger();
+    // no CTA leaves while its partner may still be sending to it
+    TL::sync_cluster();
+    // every cluster made its last claim before counting itself out, so the
+    // last one out can reset the queue for the next launch
+    if (queued && rank == 0 && threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(F.queue + 1, 1u) == (unsigned)n_clusters<TL>() - 1u) {
+        atomicExch(F.queue, 0u);
+        atomicExch(F.queue + 1, 0u);
+      }
     }
   }
 }
