@@ -107,7 +107,13 @@ struct TcMat {
 
 // Transforms tasks task0..task0+7.  ld(task, e) -> float2 input element e
 // (only called for e < R); st(task, m, float2) receives output m < R.
-template <int MODE, int R, class Ld, class St>
+// CONJ: the opposite direction from the same fragments.  The DFT matrix is
+// symmetric, so the real form of the other direction, [[Wr, Wi], [-Wi, Wr]],
+// is M with its off-diagonal blocks negated: the sign bits of every part of
+// those fragments are flipped (rounding to tf32 / bf16 is symmetric, so the
+// parts of -x are the negated parts of x).  One matrix per stage then
+// serves both directions.
+template <int MODE, int R, bool CONJ = false, class Ld, class St>
 __device__ __forceinline__ void tc_dft8(const TcMat<MODE>& M, int task0, const Ld& ld, const St& st) {
   const int lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
@@ -141,7 +147,9 @@ __device__ __forceinline__ void tc_dft8(const TcMat<MODE>& M, int task0, const L
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
-        // part q of the matrix fragment
+        // part q of the matrix fragment (sign bits of both bf16 halves
+        // flipped in the off-diagonal blocks of the opposite direction)
+        const uint32_t fl = (CONJ && mt != ks) ? 0x80008000u : 0u;
         auto A = [&](int q) {
           const uint32_t* a = &M.a[16 * q + (mt * 2 + ks) * 4];
           return a;
@@ -149,7 +157,7 @@ __device__ __forceinline__ void tc_dft8(const TcMat<MODE>& M, int task0, const L
         // the products a_i b_j with i + j <= NPART - 1, smallest first
         auto prod = [&](int i, int j) {
           const uint32_t* a = A(i);
-          const uint32_t AF[4] = {a[0], a[1], a[2], a[3]};
+          const uint32_t AF[4] = {a[0] ^ fl, a[1] ^ fl, a[2] ^ fl, a[3] ^ fl};
           mma_bf16(d[mt], AF, b[ks][0][j], b[ks][1][j]);
         };
         if constexpr (NPART == 3) {
@@ -161,7 +169,7 @@ __device__ __forceinline__ void tc_dft8(const TcMat<MODE>& M, int task0, const L
         prod(0, 1);
         float t[4] = {0.f, 0.f, 0.f, 0.f};
         const uint32_t* a = A(0);
-        const uint32_t AF[4] = {a[0], a[1], a[2], a[3]};
+        const uint32_t AF[4] = {a[0] ^ fl, a[1] ^ fl, a[2] ^ fl, a[3] ^ fl};
         mma_bf16(t, AF, b[ks][0][0], b[ks][1][0]);
         lead(mt, t);
       }
@@ -176,12 +184,14 @@ __device__ __forceinline__ void tc_dft8(const TcMat<MODE>& M, int task0, const L
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
+        // k-steps 2, 3 read imaginary parts: off-diagonal when mt == 0
+        const uint32_t fl = (CONJ && mt != (kk >= 2 ? 1 : 0)) ? 0x80000000u : 0u;
         const uint32_t* ah = &M.a[(mt * 4 + kk) * 4];
-        const uint32_t AH[4] = {ah[0], ah[1], ah[2], ah[3]};
+        const uint32_t AH[4] = {ah[0] ^ fl, ah[1] ^ fl, ah[2] ^ fl, ah[3] ^ fl};
         const uint32_t b0h = f2tf32(v[kk][0]), b1h = f2tf32(v[kk][1]);
         if constexpr (MODE == TC_TF32X3) {
           const uint32_t* al = &M.a[32 + (mt * 4 + kk) * 4];
-          const uint32_t AL[4] = {al[0], al[1], al[2], al[3]};
+          const uint32_t AL[4] = {al[0] ^ fl, al[1] ^ fl, al[2] ^ fl, al[3] ^ fl};
           const uint32_t b0l = f2tf32(v[kk][0] - __uint_as_float(b0h));
           const uint32_t b1l = f2tf32(v[kk][1] - __uint_as_float(b1h));
           mma_tf32(d[mt], AL, b0h, b1h);

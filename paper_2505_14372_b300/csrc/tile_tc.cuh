@@ -39,9 +39,11 @@ struct TileTC : Base {
   __device__ static const uint32_t* table(int m) { return g_tc_tables[MODE - 1][m]; }
   // this tile's row stages spread rows over all warps
   __device__ static void row_sync() { __syncthreads(); }
-  template <int R, int DIR>
+  // fragments of the forward R-point matrix; the inverse direction uses
+  // the same registers with the off-diagonal signs flipped (tc_dft8 CONJ)
+  template <int R>
   __device__ static void load_mat(TcMat<MODE>& M) {
-    M.load(table((R == R1 && R1 != R2 ? 0 : 2) + (DIR > 0 ? 1 : 0)));
+    M.load(table(R == R1 && R1 != R2 ? 0 : 2));
   }
 
   // ---- row strided ------------------------------------------------------
@@ -49,9 +51,8 @@ struct TileTC : Base {
   __device__ static void row_strided(float2* wave, const float2* twS, int rank, const Load& load, const Pre& pre,
                                      const Op& op) {
     const int warp = threadIdx.x >> 5;
-    TcMat<MODE> Mi, Mf;
-    if constexpr (FROM_SMEM) load_mat<R1, +1>(Mi);
-    if constexpr (TO_SMEM) load_mat<R1, -1>(Mf);
+    TcMat<MODE> M;
+    load_mat<R1>(M);
     auto sl = [&](int id, int e) {
       const int r = id / R2, col = id % R2 + R2 * e;
       return rslot(rank, col / ROWS, r, col % ROWS);
@@ -60,8 +61,8 @@ struct TileTC : Base {
     for (int q = warp; q < TS / 8; q += WARPS) {
       const int task0 = 8 * q;
       if constexpr (FROM_SMEM) {
-        tc_dft8<MODE, R1>(
-            Mi, task0, [&](int id, int e) { return wave[sl(id, e)]; },
+        tc_dft8<MODE, R1, true>(
+            M, task0, [&](int id, int e) { return wave[sl(id, e)]; },
             [&](int id, int m, float2 v) {
               if constexpr (TO_SMEM) {
                 wave[sl(id, m)] = v;
@@ -74,8 +75,8 @@ struct TileTC : Base {
         if constexpr (TO_SMEM) __syncwarp();
       }
       if constexpr (TO_SMEM) {
-        tc_dft8<MODE, R1>(
-            Mf, task0,
+        tc_dft8<MODE, R1, false>(
+            M, task0,
             [&](int id, int e) {
               const int r = id / R2, col = id % R2 + R2 * e;
               const int grow = rank * ROWS + r;
@@ -99,14 +100,14 @@ struct TileTC : Base {
   __device__ static void row_contig(float2* wave, const float2* twC, int rank) {
     const int warp = threadIdx.x >> 5;
     TcMat<MODE> M;
-    load_mat<R2, DIR>(M);
+    load_mat<R2>(M);
     auto sl = [&](int id, int e) {
       const int r = id / R1, k1 = id % R1;
       return rslot(rank, k1 / NB, r, R2 * (k1 % NB) + e);
     };
 #pragma unroll 1
     for (int q = warp; q < TC / 8; q += WARPS) {
-      tc_dft8<MODE, R2>(
+      tc_dft8<MODE, R2, (DIR > 0)>(
           M, 8 * q, [&](int id, int e) { return wave[sl(id, e)]; },
           [&](int id, int m, float2 v) {
             if constexpr (DIR > 0) {
@@ -137,14 +138,14 @@ struct TileTC : Base {
   __device__ static void col_strided(float2* wave, const float2* twS, int rank) {
     const int warp = threadIdx.x >> 5;
     TcMat<MODE> M;
-    load_mat<R1, DIR>(M);
+    load_mat<R1>(M);
     auto sl = [&](int id, int e) {
       const int n2 = id / ROWS, cc = id % ROWS;
       return cslot(rank, e / NB, n2 + R2 * (e % NB), cc);
     };
 #pragma unroll 1
     for (int q = warp; q < TS / 8; q += WARPS) {
-      tc_dft8<MODE, R1>(
+      tc_dft8<MODE, R1, (DIR > 0)>(
           M, 8 * q, [&](int id, int e) { return wave[sl(id, e)]; },
           [&](int id, int m, float2 v) {
             if constexpr (DIR < 0) {
@@ -166,9 +167,8 @@ struct TileTC : Base {
   template <bool FROM_SMEM, bool FWD, bool INV, bool WB = false, class Load, class Op>
   __device__ static void col_contig(float2* wave, const float2* twC, int rank, const Load& load, const Op& op) {
     const int warp = threadIdx.x >> 5;
-    TcMat<MODE> Mf, Mi;
-    if constexpr (FWD) load_mat<R2, -1>(Mf);
-    if constexpr (INV) load_mat<R2, +1>(Mi);
+    TcMat<MODE> M;
+    load_mat<R2>(M);
     auto sl = [&](int id, int e) {
       const int k1 = id / ROWS, cc = id % ROWS;
       return cslot(rank, k1 / NB, R2 * (k1 % NB) + e, cc);
@@ -182,8 +182,8 @@ struct TileTC : Base {
     for (int q = warp; q < TC / 8; q += WARPS) {
       const int task0 = 8 * q;
       if constexpr (FWD) {
-        tc_dft8<MODE, R2>(
-            Mf, task0, [&](int id, int e) { return wave[sl(id, e)]; },
+        tc_dft8<MODE, R2, false>(
+            M, task0, [&](int id, int e) { return wave[sl(id, e)]; },
             [&](int id, int m, float2 v) {
               if constexpr (INV) {
                 wave[sl(id, m)] = v;
@@ -197,8 +197,8 @@ struct TileTC : Base {
         if constexpr (INV) __syncwarp();
       }
       if constexpr (INV) {
-        tc_dft8<MODE, R2>(
-            Mi, task0,
+        tc_dft8<MODE, R2, true>(
+            M, task0,
             [&](int id, int e) {
               int pu, pv;
               pu_pv(id, e, pu, pv);
