@@ -9,9 +9,9 @@ adjoint, all in complex128 / float64.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants and brute-force finite differences (no worked example is printed
-in the paper).  The one part that stays "parity unpinned" is exact agreement
-with the paper's own package, whose conventions (DFT sign, normalisation,
-band-limit shape, epsilon placement) are not printed; the readings taken
-here are listed in ``ptycho.py``'s module docstring.
+in the paper).  What no test can decide is bit-level agreement with the
+paper's own package, whose conventions (DFT sign, normalisation, band-limit
+shape, epsilon placement) are not printed; the readings taken here are
+listed in ``ptycho.py``'s module docstring.
 """
 from .ptycho import *  # noqa: F401,F403
